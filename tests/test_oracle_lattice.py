@@ -1,0 +1,241 @@
+"""Pins of the oracle's lattice update: collision, streaming, halfway
+bounce-back, body forcing, boundary flux and non-equilibrium extrapolation.
+
+The references are conservation laws and closed-form flows: mass and
+momentum balance, the parabolic channel flow (exact for BGK with halfway
+bounce-back at tau = 1/2 + sqrt(3/16)), Hagen-Poiseuille, the planar
+Womersley solution, and the identity Eq. Non-equilibrium3 reduces to when
+the neighbouring fluid node is in equilibrium.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import BC_PRESSURE, BC_RCR, BC_VELOCITY, Boundary, Instance, configs, geometry, profiles
+
+CS2 = 1.0 / 3.0
+TAU_MAGIC = 0.5 + np.sqrt(3.0 / 16.0)
+
+
+def _nu(tau):
+    return CS2 * (tau - 0.5)
+
+
+def test_mass_conserved_closed_box():
+    node = geometry.closed_box(8, 9, 10)
+    inst = Instance(node=node, tau=0.7)
+    o = oracle.Oracle(inst)
+    o.set_populations(configs.random_populations(inst, 1, 1e-2))
+    fl = node.reshape(-1) == 0
+    m0 = o.populations()[:, fl].sum()
+    o.step(1000)
+    m1 = o.populations()[:, fl].sum()
+    assert abs(m1 - m0) / m0 < 1e-12
+
+
+def test_momentum_balance_periodic_box(d3q19):
+    # fully periodic: mass conserved, total momentum grows by exactly N g per step
+    node = np.zeros((5, 4, 6), dtype=np.uint8)
+    inst = Instance(node=node, tau=0.9)
+    o = oracle.Oracle(inst, periodic=7)
+    o.set_populations(configs.random_populations(inst, 2, 1e-2))
+    f0 = o.populations()
+    m0, p0 = f0.sum(), d3q19.T @ f0.sum(axis=1)
+    g = np.array([1e-5, -2e-5, 3e-5])
+    o.set_body_force(g)
+    o.step(50)
+    f1 = o.populations()
+    N = node.size
+    assert abs(f1.sum() - m0) / m0 < 1e-13
+    assert np.allclose(d3q19.T @ f1.sum(axis=1), p0 + 50 * N * g, rtol=1e-10, atol=1e-14)
+
+
+def _channel(tau, ny=10, g=1e-6, steps=20000):
+    node = geometry.plates_channel(1, ny, 1)
+    o = oracle.Oracle(Instance(node=node, tau=tau), periodic=1 | 4)
+    o.set_body_force([g, 0, 0])
+    o.step(steps)
+    P, jx, jy, jz = o.macros()
+    u = jx.reshape(ny) + g / 2
+    y = np.arange(ny) + 0.5
+    ana = g / (2 * _nu(tau)) * (y - 1.0) * (ny - 1.0 - y)   # walls halfway, at y = 1 and ny - 1
+    return y[1:-1], u[1:-1], ana[1:-1]
+
+
+@pytest.mark.parametrize("tau", [TAU_MAGIC, 0.8, 1.2])
+def test_channel_profile_is_parabola(tau):
+    y, u, ana = _channel(tau)
+    c = np.polyfit(y, u, 2)
+    assert np.abs(np.polyval(c, y) - u).max() / u.max() < 1e-10
+    assert c[0] == pytest.approx(-1e-6 / (2 * _nu(tau)), rel=1e-8)   # curvature set by g / nu
+
+
+def test_channel_exact_at_magic_tau():
+    y, u, ana = _channel(TAU_MAGIC)
+    assert np.abs(u - ana).max() / ana.max() < 1e-9
+    y, u, ana = _channel(0.8)
+    assert np.abs(u - ana).max() / ana.max() > 1e-3   # a slip elsewhere, as expected for BGK
+
+
+@pytest.mark.parametrize("R", [4, 6, 8])
+def test_tube_hagen_poiseuille(R):
+    n = 2 * R + 4
+    node = geometry.periodic_tube(n, n, 1, R)
+    o = oracle.Oracle(Instance(node=node, tau=TAU_MAGIC), periodic=4)
+    g = 1e-6
+    o.set_body_force([0, 0, g])
+    o.step(int(6 * R * R / _nu(TAU_MAGIC)))
+    fl = node.reshape(-1) == 0
+    Q = (o.macros()[3][fl] + g / 2).sum()
+    R_eff = np.sqrt(fl.sum() / np.pi)     # radius of the staircase cross-section's area
+    assert Q == pytest.approx(np.pi * g * R_eff ** 4 / (8 * _nu(TAU_MAGIC)), rel=0.05)
+
+
+def test_planar_womersley_second_order():
+    errs = []
+    for ny, T in ((10, 125), (18, 500), (34, 2000)):          # diffusive scaling, alpha fixed
+        node = geometry.plates_channel(1, ny, 1)
+        o = oracle.Oracle(Instance(node=node, tau=TAU_MAGIC), periodic=1 | 4)
+        g0, w, nu = 1e-6, 2 * np.pi / T, _nu(TAU_MAGIC)
+        y = np.arange(ny) + 0.5
+        k = np.sqrt(1j * w / nu)
+        U = g0 / (1j * w) * (1 - np.cosh(k * (y - ny / 2)) / np.cosh(k * (ny - 2) / 2))
+        err = mx = 0.0
+        for n in range(6 * T):
+            b = g0 * np.cos(w * n)
+            o.set_body_force([b, 0, 0])
+            if n >= 5 * T and n % 5 == 0:
+                u = o.macros()[1].reshape(ny)[1:-1] + b / 2
+                ua = (U * np.exp(1j * w * n)).real[1:-1]
+                err, mx = max(err, np.abs(u - ua).max()), max(mx, np.abs(ua).max())
+            o.step(1)
+        errs.append(err / mx)
+    assert errs[0] < 5e-3
+    assert errs[0] / errs[1] > 3.5 and errs[1] / errs[2] > 3.5, errs
+
+
+def test_flux_of_uniform_flow():
+    # f(t_0) = f^eq(P_ref, u e_z) everywhere: the boundary flow fed to the 0D
+    # models is the area-mean velocity u, positive into the domain (inlet +u,
+    # outlet -u), with the mean gauge pressure 0
+    inst = configs.pressure_tube(12, 12, 10, 4.0, 0.8, 0.0, 0.0)
+    o = oracle.Oracle(inst)
+    N = o.N
+    feq = oracle.feq(CS2, [0, 0, 0.01])
+    o.set_populations(np.repeat(feq[:, None], N, axis=1))
+    o.step(1)
+    w = o.waves()[0]
+    assert w[1] == pytest.approx(0.01, rel=1e-13) and w[5] == pytest.approx(-0.01, rel=1e-13)
+    assert abs(w[2]) < 1e-15 and abs(w[6]) < 1e-15
+    s = o.state_0d(0)
+    assert s[1] == pytest.approx(0.01 * o.n_xf(0), rel=1e-13)   # literal Q = sum over the layer
+
+
+def test_nee_equilibrium_neighbour_identity():
+    # with x_f in equilibrium and no force, Eq. Non-equilibrium3 gives
+    # f_i(x_f, t_1) = f^eq_i(P*, v*) for every population entering from dOmega_2
+    v0 = np.array([0.0, 0.0, 0.02])
+    p_in, p_out = 3e-3, -2e-3
+    inst = configs.pressure_tube(12, 12, 10, 4.0, 0.8, p_in, p_out)
+    o = oracle.Oracle(inst)
+    feq0 = oracle.feq(CS2, v0)
+    o.set_populations(np.repeat(feq0[:, None], o.N, axis=1))
+    o.step(1)
+    f = o.populations()
+    nx, ny, nz = inst.shape
+    fin = oracle.feq(CS2 + p_in, v0)
+    fout = oracle.feq(CS2 + p_out, v0)
+    node = inst.node
+    up = [5, 11, 14, 15, 18]      # directions with e_z = +1 in the documented order
+    dn = [6, 12, 13, 16, 17]      # e_z = -1
+    checked = 0
+    for y in range(ny):
+        for x in range(nx):
+            for i in up:
+                ex, ey = [0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0][i], \
+                         [0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1][i]
+                if node[1, y, x] == 0 and 0 <= x - ex < nx and 0 <= y - ey < ny and node[0, y - ey, x - ex] == 2:
+                    assert f[i, x + nx * (y + ny * 1)] == pytest.approx(fin[i], rel=1e-14)
+                    checked += 1
+            for i in dn:
+                ex, ey = [0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0][i], \
+                         [0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1][i]
+                if node[nz - 2, y, x] == 0 and 0 <= x - ex < nx and 0 <= y - ey < ny and node[nz - 1, y - ey, x - ex] == 3:
+                    assert f[i, x + nx * (y + ny * (nz - 2))] == pytest.approx(fout[i], rel=1e-14)
+                    checked += 1
+    assert checked == o.n_links(0) + o.n_links(1)
+
+
+def test_pressure_driven_tube_matches_force_driven():
+    # Poiseuille flow between two constant-pressure ends coupled by Eq.
+    # Non-equilibrium3: the interior pressure is linear, and the cross-section
+    # velocity equals the body-force-driven flow with g = -dP/dz
+    R, nz, dp = 4, 24, 1e-4
+    n = 2 * R + 4
+    o = oracle.Oracle(configs.pressure_tube(n, n, nz, R, TAU_MAGIC, dp / 2, -dp / 2))
+    o.step(1600)
+    P, jx, jy, jz = o.macros()
+    Pc = P.reshape(nz, n, n)[:, n // 2, n // 2]
+    zz = np.arange(4, nz - 4)
+    c = np.polyfit(zz, Pc[4:nz - 4], 1)
+    assert np.abs(np.polyval(c, zz) - Pc[4:nz - 4]).max() < 2e-3 * dp
+    g = -(Pc[nz // 2 + 4] - Pc[nz // 2 - 4]) / 8.0       # interior gradient at mid-length
+    node2 = geometry.periodic_tube(n, n, 1, R)
+    o2 = oracle.Oracle(Instance(node=node2, tau=TAU_MAGIC), periodic=4)
+    o2.set_body_force([0, 0, g])
+    o2.step(1600)
+    m = node2[0] == 0
+    u1 = jz.reshape(nz, n, n)[nz // 2][m]
+    u2 = o2.macros()[3].reshape(n, n)[m] + g / 2
+    assert np.abs(u1 - u2).max() / u2.max() < 1e-3
+    w = o.waves()[-1]
+    assert abs(w[1] + w[5]) / w[1] < 1e-3               # steady: inflow = outflow
+
+
+def test_velocity_inlet_mass_balance():
+    # prescribed plug inflow at the inlet, RCR outlet.  At steady state the
+    # momentum density n.j integrated over the inlet layer equals that over the
+    # outlet layer (mass balance; Q_u = n.j / sum f, sum f = P / c_s^2), the
+    # plug is slowed only by the no-slip rim, and the Windkessel chamber
+    # settles at P_w = R_d Q_out.
+    nx = ny = 12
+    inst = configs.pressure_tube(nx, ny, 16, 4.0, 0.8, 0.0, 0.0)
+    u = 0.005
+    n_in = inst.boundary_nodes(0).size
+    inst.boundaries[0] = Boundary(BC_VELOCITY, 2, +1, [0.0], profile=profiles.plug_profile(n_in, u))
+    inst.boundaries[1] = Boundary(BC_RCR, 2, -1, [0.05, 20.0, 1.0, 0.0])
+    o = oracle.Oracle(inst)
+    o.step(3000)
+    w = o.waves()[-1]
+    j_in = w[1] * (1 + w[2] / CS2)
+    j_out = -w[5] * (1 + w[6] / CS2)
+    assert j_in == pytest.approx(j_out, rel=2e-3)      # layer means of a ratio: approximate
+    assert 0.7 * u < w[1] < u
+    s = o.state_0d(1)
+    assert s[4] == pytest.approx(-1.0 * w[5], rel=1e-9)      # P_w = R_d Q_out at steady state
+
+
+def test_lv_inlet_hybrid_switching_in_lattice():
+    # the hybrid ODE-Dirichlet inlet in a small tube: after start-up the valve
+    # opens and closes once per beat; while open the inlet pressure follows the
+    # ventricular pressure (Section 3.2: inlet and LV pressure coincide in
+    # systole); after closure the smoothed Dirichlet condition brings the
+    # inflow to zero within N_S steps
+    T = 600
+    inst = configs.lv_tube(period=T)
+    o = oracle.Oracle(inst)
+    o.step(5 * T)
+    w = o.waves()
+    op = w[:, 4]
+    opens = np.flatnonzero(np.diff(op) > 0) + 1
+    closes = np.flatnonzero(np.diff(op) < 0) + 1
+    for beat in (3, 4):
+        lo, hi = beat * T, (beat + 1) * T
+        assert ((opens >= lo) & (opens < hi)).sum() == 1
+        assert ((closes >= lo) & (closes < hi)).sum() == 1
+    sl = slice(3 * T, 5 * T)
+    Pin, Pv, Qin, opn = w[sl, 2], w[sl, 3], w[sl, 1], w[sl, 4] == 1
+    assert np.abs(Pin[opn] - Pv[opn]).max() < 0.1 * Pv.max()
+    n_s = int(inst.boundaries[0].params[2])
+    c = closes[closes >= 3 * T][0]
+    assert np.abs(w[c + n_s + 5: c + n_s + 50, 1]).max() < 0.05 * Qin.max()
