@@ -1,0 +1,186 @@
+/*
+ * liblbm — GB300 (sm_103a) implementation of the per-step hot path of the
+ * direct 0D-3D coupled lattice Boltzmann method of arXiv 2112.05258:
+ * D3Q19 stream-collide with halfway bounce-back, 0D-coupled boundary nodes
+ * set by non-equilibrium extrapolation from RCR Windkessel / hybrid
+ * left-ventricle ODEs, and the penalty immersed-boundary exchange with
+ * Lagrangian wall nodes.
+ *
+ * Conventions (all calls):
+ *  - Every call returns an lbm_status; nothing throws across this boundary.
+ *    On failure, lbm_last_error(h) describes the cause.  Arguments are
+ *    validated before any device work is enqueued.
+ *  - The handle owns all device memory it allocates; no pointer passed in is
+ *    retained after the call returns (host arrays are copied).
+ *  - Lattice node (x, y, z) of an nx*ny*nz box has the flat index
+ *    x + nx*(y + ny*z) and sits at (x+0.5, y+0.5, z+0.5) in lattice units
+ *    (dx = dt = 1).  Node codes: 0 fluid (Omega), 1 rigid wall (halfway
+ *    bounce-back), 2+k node of 0D boundary k (dOmega_2).
+ *  - Population order i = 0..18: rest; +x, -x, +y, -y, +z, -z;
+ *    (1,1,0), (-1,-1,0), (1,-1,0), (-1,1,0), (1,0,1), (-1,0,-1), (1,0,-1),
+ *    (-1,0,1), (0,1,1), (0,-1,-1), (0,1,-1), (0,-1,1).  Weights 1/3, 1/18,
+ *    1/36 (He & Luo incompressible model, Section 2.1.1).
+ *  - Work is enqueued on the stream given at creation; calls that return
+ *    data to the host synchronise that stream.
+ *  - Pressures in the 0D interface are gauge pressures, P - P_ref with
+ *    P_ref = c_s^2 = 1/3 the lattice pressure at rest.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,      /* invalid argument; nothing was enqueued */
+    LBM_ERR_CUDA = -2,     /* a CUDA call failed; see lbm_last_error */
+    LBM_ERR_OOM = -3,      /* device allocation failed */
+    LBM_ERR_UNSTABLE = -4, /* device status word: NaN/Inf or |v| > 0.3 seen; state stays readable */
+    LBM_ERR_STATE = -5     /* call not valid in the handle's current state */
+} lbm_status;
+
+typedef enum {
+    LBM_F32 = 0,  /* populations stored as FP32 deviations f_i - w_i, FP32 arithmetic */
+    LBM_F16 = 1,  /* stored as FP16 deviations (round to nearest even), FP32 arithmetic */
+    LBM_BF16 = 2, /* stored as BF16 deviations (round to nearest even), FP32 arithmetic */
+    LBM_F64 = 3   /* stored and computed in FP64 (parity instantiation) */
+} lbm_precision;
+
+typedef enum {
+    LBM_BC_VELOCITY = 0, /* prescribed normal velocity, velocity-type coupling (Section 2.2) */
+    LBM_BC_RCR = 1,      /* RCR Windkessel, pressure-type coupling (Eqs. rightbc, rightQ) */
+    LBM_BC_LV = 2,       /* hybrid LV elastance inlet (Eq. LVE, Section 2.2.1) */
+    LBM_BC_PRESSURE = 3  /* constant gauge pressure, pressure-type coupling */
+} lbm_bc_kind;
+
+/* One 0D-coupled boundary.  Its inward unit normal is sign * e_axis.
+ * params by kind (host, copied):
+ *   VELOCITY: {omega}; profile = n_profile x {u_mean, c_re, c_im} in raster
+ *             order of the boundary's nodes (n_profile must equal the node
+ *             count); prescribed normal velocity u_mean + Re{c e^{i omega t}}.
+ *   RCR:      {R_p, C, R_d, P_w0}   (Z_w = R_p, C_w = C, R_w = R_d)
+ *   LV:       {period, P_la, N_S, P_v0}; elastance = period x {E, dE/dt} at
+ *             integer steps (the C_v(t) = 1/E input of Algorithm 1)
+ *   PRESSURE: {p_gauge}                                                   */
+typedef struct {
+    int kind;
+    int axis; /* 0 = x, 1 = y, 2 = z */
+    int sign; /* +1 or -1 */
+    int n_params;
+    const double *params;
+    int64_t n_profile;
+    const double *profile;
+    int period;
+    const double *elastance;
+} lbm_boundary_desc;
+
+/* One lattice instance.  Several instances form a batch advanced together. */
+typedef struct {
+    int nx, ny, nz;
+    const uint8_t *node; /* host, nx*ny*nz node codes (copied) */
+    double tau;          /* BGK relaxation time, > 0.5 (Eq. tau) */
+    int q_scale;         /* 1: 0D models see Q/A (area-mean velocity); 0: literal Q */
+    int n_bc;            /* <= 8 */
+    const lbm_boundary_desc *bc;
+    /* Lagrangian wall nodes for the penalty immersed boundary (Eqs. LagForce,
+     * interpolation, EulForce); n_ib = 0 for none.  Host arrays, copied. */
+    int64_t n_ib;
+    const double *ib_X0;      /* n_ib x 3 reference positions */
+    const double *ib_dA;      /* n_ib area weights */
+    const double *ib_ks;      /* n_ib spring stiffness (per area) */
+    const uint8_t *ib_pinned; /* n_ib, 1 = held at X0 */
+    double ib_alpha, ib_beta; /* penalty gains, both < 0 */
+    double ib_ms;             /* wall mass per area */
+} lbm_instance_desc;
+
+typedef struct {
+    int precision; /* lbm_precision */
+    int n_instances;
+    const lbm_instance_desc *inst;
+    void *stream;      /* cudaStream_t to enqueue on; NULL: the library creates one */
+    int device;        /* CUDA device ordinal */
+    int graph_steps;   /* steps per captured CUDA graph (even, >= 2); 0 = 64 */
+    int wave_capacity; /* waveform ring-buffer length in steps; 0 = 8192 */
+    int block_size;    /* threads per block of the stream-collide kernel, multiple of 32 in [32, 256]; 0 = 256 */
+} lbm_config;
+
+typedef struct lbm_handle lbm_handle;
+
+typedef struct {
+    int64_t fluid_cells;  /* cells of Omega updated per step (all instances) */
+    int64_t stored_cells; /* cells with population storage (fluid + boundary + in-row walls) */
+    int64_t box_cells;
+    int64_t band_cells;   /* fluid cells within the immersed-boundary kernel support */
+    int64_t ib_nodes;
+    int64_t links;        /* boundary links (x_b, i) set by extrapolation each step */
+    int64_t steps;        /* steps taken so far */
+    int64_t device_bytes; /* device memory held by the handle */
+    int precision;
+    int bytes_per_population;
+} lbm_info_t;
+
+/* Builds the compact row layout of every instance, copies inputs, and
+ * initialises the fluid at rest (f_i = w_i, P = P_ref, v = 0; Section 2.3.2)
+ * with the 0D states from their params.  *out receives the handle. */
+lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out);
+
+/* Replaces the params of boundary bc of instance inst (same layout as in
+ * lbm_boundary_desc; for LV/RCR the state entries P_v0 / P_w0 are ignored
+ * after creation).  Enqueued in stream order. */
+lbm_status lbm_set_0d_params(lbm_handle *h, int inst, int bc, const double *p, int np);
+
+/* Sets f_i(x, t_0) of every fluid node of instance inst from a host array of
+ * 19 x (nx*ny*nz) doubles (population-major, box order); non-fluid entries
+ * are ignored.  The state is laid out so that the next step starts from it. */
+lbm_status lbm_init_populations(lbm_handle *h, int inst, const double *f);
+
+/* Advances all instances by n steps (Algorithm 1).  Asynchronous: returns
+ * after enqueueing (as CUDA graphs of graph_steps steps where possible). */
+lbm_status lbm_step(lbm_handle *h, int64_t n);
+
+/* Waits for the stream; returns LBM_ERR_UNSTABLE if the device status word
+ * recorded NaN/Inf or |v| > 0.3 since creation. */
+lbm_status lbm_sync(lbm_handle *h);
+
+/* Host outputs, box order, nx*ny*nz doubles each (non-fluid nodes 0):
+ * P = c_s^2 sum_i f_i and j = sum_i e_i f_i of the current f(t_n)
+ * (Eqs. rho, v before the force term of step n is added). */
+lbm_status lbm_read_fields(lbm_handle *h, int inst, double *P, double *jx, double *jy, double *jz);
+
+/* Host output: f_i(x, t_n) as 19 x (nx*ny*nz) doubles (non-fluid 0). */
+lbm_status lbm_read_populations(lbm_handle *h, int inst, double *f);
+
+/* 8 doubles: {t_{n+1}, Q(t_n), Q_u(t_n), Pbar_gauge(t_n), state (P_w, P_v
+ * or P*-P_ref), C_v(t_{n+1}) P_v (LV) or 0, valve_open, T_d}. */
+lbm_status lbm_read_0d_state(lbm_handle *h, int inst, int bc, double *out);
+
+/* The last min(steps, capacity, max_rows) steps of instance inst: rows of
+ * 1 + 4*n_bc doubles {step, then per boundary Q_u, Pbar_gauge, state,
+ * valve_open}; *rows receives the row count. */
+lbm_status lbm_read_waveforms(lbm_handle *h, int inst, double *out, int64_t max_rows, int64_t *rows);
+
+/* Wall-node arrays of instance inst (n_ib x 3 doubles each; NULL to skip):
+ * position X, velocity V_s, force on the fluid F, interpolated V_f. */
+lbm_status lbm_read_ib(lbm_handle *h, int inst, double *X, double *Vs, double *F, double *Vf);
+lbm_status lbm_set_ib_state(lbm_handle *h, int inst, const double *X, const double *Vs);
+
+/* Kernel timing for roofline measurement.  While enabled, lbm_step launches
+ * its kernels directly (no graph) and brackets every stream-collide launch
+ * with CUDA events recorded on the handle's stream.  lbm_get_kernel_time
+ * synchronises and returns the number of timed launches and their summed
+ * duration in milliseconds since timing was (re-)enabled. */
+lbm_status lbm_set_kernel_timing(lbm_handle *h, int enable);
+lbm_status lbm_get_kernel_time(lbm_handle *h, int64_t *launches, double *total_ms);
+
+lbm_status lbm_get_info(lbm_handle *h, lbm_info_t *info);
+const char *lbm_last_error(const lbm_handle *h);
+void lbm_destroy(lbm_handle *h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -1,0 +1,631 @@
+// C-ABI entry points of liblbm (see include/lbm.h for the contract of each).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_internal.h"
+#include "lbm_kernels.h"
+
+namespace lbm {
+std::string build_layout(const lbm_config *cfg, Layout &L);
+}
+
+using namespace lbm;
+
+struct lbm_handle {
+    int device = 0;
+    int prec = 0;
+    int sbytes = 4;  // bytes per stored population
+    int rbytes = 4;  // bytes of the compute type
+    int block = 256;
+    int graph_steps = 64;
+    int wave_cap = 8192;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    Layout L;
+    std::vector<lbm_instance_desc> inst;  // shapes only (pointers not retained)
+    // device buffers
+    void *f[2] = {nullptr, nullptr};
+    int parity = 0;  // f[parity] holds the resident post-collision state
+    void *b = nullptr, *aux = nullptr, *vband = nullptr;
+    uint32_t *flags = nullptr;
+    RowInfo *rows = nullptr;
+    int32_t *chunk_row = nullptr, *rowid = nullptr;
+    double *omega = nullptr;
+    long long *step_dev = nullptr;
+    unsigned *status = nullptr;
+    BcParam *bc_par = nullptr;
+    BcState *bc_state = nullptr;
+    int32_t *xf = nullptr, *lk_xb = nullptr, *lk_xf = nullptr, *lk_node = nullptr, *lk_xfi = nullptr;
+    uint8_t *lk_i = nullptr;
+    double *profile = nullptr, *etab = nullptr, *v0 = nullptr, *wave = nullptr;
+    InstParam *inst_dev = nullptr;
+    double *partial = nullptr;
+    int32_t *red_bc = nullptr, *red_chunk = nullptr, *app_bc = nullptr, *app_chunk = nullptr;
+    int32_t *band = nullptr, *node_inst = nullptr;
+    double *ibX = nullptr, *ibVs = nullptr, *ibI = nullptr, *ibF = nullptr, *ibVf = nullptr;
+    double *ibX0 = nullptr, *ibdA = nullptr, *ibks = nullptr;
+    uint8_t *ibpin = nullptr;
+    double *rd_f19 = nullptr, *rd_mac = nullptr;  // read-out scratch (allocated on first read)
+    std::vector<void *> allocs;
+    int64_t bytes = 0;
+    KParams kp{};
+    BcKParams bp{};
+    IbKParams ibp{};
+    int64_t steps = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    // kernel timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    size_t ev_used = 0;
+    int64_t timed_launches = 0;
+    double timed_ms = 0.0;
+    std::string err;
+};
+
+namespace {
+
+lbm_status fail(lbm_handle *h, lbm_status s, const std::string &msg) {
+    if (h) h->err = msg;
+    return s;
+}
+
+#define CK(h, call)                                                                                 \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return fail(h, e_ == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,            \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                       \
+    } while (0)
+
+template <class T> cudaError_t dalloc(lbm_handle *h, T **p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+    if (e != cudaSuccess) return e;
+    h->allocs.push_back(q);
+    h->bytes += (int64_t)(count * sizeof(T));
+    *p = static_cast<T *>(q);
+    return cudaSuccess;
+}
+
+cudaError_t dalloc_bytes(lbm_handle *h, void **p, size_t bytes) {
+    uint8_t *q = nullptr;
+    cudaError_t e = dalloc(h, &q, bytes);
+    *p = q;
+    return e;
+}
+
+template <class T> cudaError_t upload(lbm_handle *h, T **p, const std::vector<T> &v) {
+    cudaError_t e = dalloc(h, p, v.size());
+    if (e != cudaSuccess) return e;
+    if (v.empty()) return cudaSuccess;
+    return cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+lbm_status check_config(const lbm_config *cfg, std::string &why) {
+    if (!cfg) return why = "null config", LBM_ERR_ARG;
+    if (cfg->precision < 0 || cfg->precision > 3) return why = "precision out of range", LBM_ERR_ARG;
+    if (cfg->n_instances <= 0 || !cfg->inst) return why = "no instances", LBM_ERR_ARG;
+    if (cfg->graph_steps < 0 || (cfg->graph_steps % 2) != 0) return why = "graph_steps must be even", LBM_ERR_ARG;
+    if (cfg->block_size != 0 && (cfg->block_size < 32 || cfg->block_size > 256 || cfg->block_size % 32))
+        return why = "block_size must be a multiple of 32 in [32, 256]", LBM_ERR_ARG;
+    for (int q = 0; q < cfg->n_instances; q++) {
+        const lbm_instance_desc &d = cfg->inst[q];
+        if (d.nx < 1 || d.ny < 1 || d.nz < 1 || !d.node) return why = "bad instance shape or node array", LBM_ERR_ARG;
+        if ((double)d.nx * d.ny * d.nz > 2.0e9) return why = "instance too large", LBM_ERR_ARG;
+        if (!(d.tau > 0.5)) return why = "tau must exceed 1/2", LBM_ERR_ARG;
+        if (d.n_bc < 0 || d.n_bc > MAX_BC || (d.n_bc && !d.bc)) return why = "n_bc out of range", LBM_ERR_ARG;
+        const int64_t nbox = (int64_t)d.nx * d.ny * d.nz;
+        for (int64_t c = 0; c < nbox; c++)
+            if (d.node[c] > 1 + d.n_bc) return why = "node code refers to an undeclared boundary", LBM_ERR_ARG;
+        for (int k = 0; k < d.n_bc; k++) {
+            const lbm_boundary_desc &b = d.bc[k];
+            if (b.kind < 0 || b.kind > 3) return why = "boundary kind out of range", LBM_ERR_ARG;
+            if (b.axis < 0 || b.axis > 2 || (b.sign != 1 && b.sign != -1)) return why = "bad boundary normal", LBM_ERR_ARG;
+            static const int need[4] = {1, 4, 4, 1};
+            if (b.n_params < need[b.kind] || !b.params) return why = "too few boundary params", LBM_ERR_ARG;
+            if (b.kind == LBM_BC_RCR && (!(b.params[1] > 0) || !(b.params[2] > 0)))
+                return why = "RCR needs C > 0 and R_d > 0", LBM_ERR_ARG;
+            if (b.kind == LBM_BC_LV) {
+                if (b.period <= 0 || !b.elastance || (int)b.params[0] != b.period)
+                    return why = "LV period and elastance table disagree", LBM_ERR_ARG;
+                for (int t = 0; t < b.period; t++)
+                    if (!(b.elastance[2 * t] > 0)) return why = "elastance must be positive", LBM_ERR_ARG;
+                if (!(b.params[2] > 0)) return why = "N_S must be positive", LBM_ERR_ARG;
+            }
+        }
+        if (d.n_ib < 0 || (d.n_ib > 0 && (!d.ib_X0 || !d.ib_dA || !d.ib_ks || !d.ib_pinned)))
+            return why = "bad immersed-boundary arrays", LBM_ERR_ARG;
+        if (d.n_ib > 0 && !(d.ib_ms > 0)) return why = "wall mass must be positive", LBM_ERR_ARG;
+        for (int64_t s = 0; s < d.n_ib; s++)
+            for (int a = 0; a < 3; a++) {
+                const int n[3] = {d.nx, d.ny, d.nz};
+                const double X = d.ib_X0[3 * s + a];
+                if (!(X >= 0.0 && X <= (double)n[a])) return why = "wall node outside the box", LBM_ERR_ARG;
+            }
+    }
+    return LBM_OK;
+}
+
+lbm_status launch_step(lbm_handle *h, bool timed) {
+    void *fin = h->f[h->parity], *fout = h->f[1 - h->parity];
+    if (h->ibp.n_nodes) CK(h, launch_ib(h->prec, fin, h->kp, h->ibp, h->stream));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (timed) {
+        if (h->ev_used + 2 > h->ev.size()) {
+            // harvest what has been recorded so far
+            CK(h, cudaStreamSynchronize(h->stream));
+            for (size_t k = 0; k + 1 < h->ev_used; k += 2) {
+                float ms = 0.f;
+                CK(h, cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1]));
+                h->timed_ms += ms;
+            }
+            h->ev_used = 0;
+        }
+        e0 = h->ev[h->ev_used++];
+        e1 = h->ev[h->ev_used++];
+        CK(h, cudaEventRecord(e0, h->stream));
+    }
+    CK(h, launch_stream_collide(h->prec, fin, fout, h->kp, h->block, h->stream));
+    if (timed) {
+        CK(h, cudaEventRecord(e1, h->stream));
+        h->timed_launches++;
+    }
+    CK(h, launch_boundary(h->prec, fout, h->kp, h->bp, h->stream));
+    h->parity ^= 1;
+    return LBM_OK;
+}
+
+lbm_status ensure_graph(lbm_handle *h) {
+    const int par = h->parity;
+    if (h->graph[par]) return LBM_OK;
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    lbm_status st = LBM_OK;
+    for (int k = 0; k < h->graph_steps && st == LBM_OK; k++) st = launch_step(h, false);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    h->parity = par;  // capture does not run anything
+    if (st != LBM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    CK(h, e);
+    e = cudaGraphInstantiate(&h->graph[par], g, 0);
+    cudaGraphDestroy(g);
+    CK(h, e);
+    return LBM_OK;
+}
+
+lbm_status read_gather(lbm_handle *h) {
+    const size_t n = (size_t)h->L.n_stored;
+    if (!h->rd_f19) CK(h, dalloc(h, &h->rd_f19, 19 * n));
+    if (!h->rd_mac) CK(h, dalloc(h, &h->rd_mac, 4 * n));
+    CK(h, launch_gather(h->prec, h->f[h->parity], h->kp, h->rd_f19, h->rd_mac, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+bool bad_inst(lbm_handle *h, int inst) { return !h || inst < 0 || inst >= (int)h->inst.size(); }
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
+    if (!out) return LBM_ERR_ARG;
+    *out = nullptr;
+    std::string why;
+    if (check_config(cfg, why) != LBM_OK) {
+        fprintf(stderr, "lbm_create: %s\n", why.c_str());
+        return LBM_ERR_ARG;
+    }
+    lbm_handle *h = new lbm_handle();
+    h->device = cfg->device;
+    h->prec = cfg->precision;
+    static const int sb[4] = {4, 2, 2, 8};
+    h->sbytes = sb[h->prec];
+    h->rbytes = h->prec == LBM_F64 ? 8 : 4;
+    h->block = cfg->block_size ? cfg->block_size : 256;
+    h->graph_steps = cfg->graph_steps ? cfg->graph_steps : 64;
+    h->wave_cap = cfg->wave_capacity > 0 ? cfg->wave_capacity : 8192;
+    h->inst.assign(cfg->inst, cfg->inst + cfg->n_instances);
+    for (auto &d : h->inst) {
+        d.node = nullptr;
+        d.bc = nullptr;
+        d.ib_X0 = d.ib_dA = d.ib_ks = nullptr;
+        d.ib_pinned = nullptr;
+    }
+    auto bail = [&](lbm_status s, const std::string &m) {
+        fprintf(stderr, "lbm_create: %s\n", m.c_str());
+        lbm_destroy(h);
+        return s;
+    };
+    std::string e = build_layout(cfg, h->L);
+    if (!e.empty()) return bail(LBM_ERR_ARG, e);
+    Layout &L = h->L;
+    if (cudaSetDevice(h->device) != cudaSuccess) return bail(LBM_ERR_CUDA, "cudaSetDevice failed");
+    if (cfg->stream) {
+        h->stream = static_cast<cudaStream_t>(cfg->stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(LBM_ERR_CUDA, "stream creation failed");
+        h->own_stream = true;
+    }
+    const size_t n = (size_t)L.n_stored;
+    auto ck = [&](cudaError_t ce, const char *what) -> bool {
+        if (ce == cudaSuccess) return true;
+        h->err = std::string(what) + ": " + cudaGetErrorString(ce);
+        return false;
+    };
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; k++) {
+        ok = ck(dalloc_bytes(h, &h->f[k], (size_t)NQ * n * h->sbytes), "populations");
+        if (ok) ok = ck(cudaMemset(h->f[k], 0, (size_t)NQ * n * h->sbytes), "memset");
+    }
+    if (ok) ok = ck(dalloc_bytes(h, &h->b, 3 * n * h->rbytes), "b") && ck(cudaMemset(h->b, 0, 3 * n * h->rbytes), "memset");
+    if (ok) ok = ck(dalloc_bytes(h, &h->aux, 4 * n * h->rbytes), "aux") && ck(cudaMemset(h->aux, 0, 4 * n * h->rbytes), "memset");
+    if (ok) ok = ck(upload(h, &h->flags, L.flags), "flags");
+    if (ok) ok = ck(upload(h, &h->rows, L.rows), "rows");
+    if (ok) ok = ck(upload(h, &h->chunk_row, L.chunk_row), "chunks");
+    if (ok) ok = ck(upload(h, &h->rowid, L.rowid), "rowid");
+    std::vector<double> om;
+    for (auto &ip : L.inst) om.push_back(ip.omega);
+    if (ok) ok = ck(upload(h, &h->omega, om), "omega");
+    if (ok) ok = ck(upload(h, &h->inst_dev, L.inst), "instances");
+    long long minus1 = -1;
+    if (ok) ok = ck(dalloc(h, &h->step_dev, 1), "step") &&
+                 ck(cudaMemcpy(h->step_dev, &minus1, sizeof minus1, cudaMemcpyHostToDevice), "step");
+    if (ok) ok = ck(dalloc(h, &h->status, 1), "status") && ck(cudaMemset(h->status, 0, sizeof(unsigned)), "status");
+    // 0D boundaries
+    std::vector<BcState> st(L.bc.size());
+    for (size_t k = 0; k < L.bc.size(); k++) {
+        memset(&st[k], 0, sizeof(BcState));
+        if (L.bc[k].kind == BC_RCR) st[k].Pw = L.bc[k].par[3];
+        if (L.bc[k].kind == BC_LV) {
+            st[k].Pv = L.bc[k].par[3];
+            st[k].Td = -1e300;
+        }
+    }
+    std::vector<BcState> st2(st);
+    st2.insert(st2.end(), st.begin(), st.end());  // [2][n_bc]: read n & 1, write (n + 1) & 1
+    if (ok) ok = ck(upload(h, &h->bc_par, L.bc), "bc") && ck(upload(h, &h->bc_state, st2), "bc state");
+    if (ok) ok = ck(dalloc(h, &h->partial, 2 * std::max<size_t>(1, (size_t)L.n_partial)), "partials") &&
+                 ck(upload(h, &h->red_bc, L.red_bc), "tables") && ck(upload(h, &h->red_chunk, L.red_chunk), "tables") &&
+                 ck(upload(h, &h->app_bc, L.app_bc), "tables") && ck(upload(h, &h->app_chunk, L.app_chunk), "tables");
+    if (ok) ok = ck(upload(h, &h->xf, L.xf), "xf") && ck(upload(h, &h->lk_xb, L.lk_xb), "links") &&
+                 ck(upload(h, &h->lk_xf, L.lk_xf), "links") && ck(upload(h, &h->lk_node, L.lk_node), "links") &&
+                 ck(upload(h, &h->lk_xfi, L.lk_xfi), "links") && ck(upload(h, &h->lk_i, L.lk_i), "links") &&
+                 ck(upload(h, &h->profile, L.profile), "profile") && ck(upload(h, &h->etab, L.etab), "etab");
+    if (ok) ok = ck(dalloc(h, &h->v0, 3 * std::max<size_t>(1, L.xf.size())), "v0") &&
+                 ck(cudaMemset(h->v0, 0, 3 * std::max<size_t>(1, L.xf.size()) * sizeof(double)), "v0");
+    const size_t nwave = (size_t)h->wave_cap * std::max<size_t>(1, L.bc.size()) * 4;
+    if (ok) ok = ck(dalloc(h, &h->wave, nwave), "wave") && ck(cudaMemset(h->wave, 0, nwave * sizeof(double)), "wave");
+    // immersed boundary
+    const size_t ns = L.ib_dA.size();
+    if (ok && ns) {
+        std::vector<int32_t> ni;
+        for (size_t q = 0; q < L.inst.size(); q++)
+            for (int s = 0; s < L.inst[q].n_ib; s++) ni.push_back((int32_t)q);
+        std::vector<double> zero(3 * ns, 0.0);
+        ok = ck(upload(h, &h->band, L.band), "band") && ck(upload(h, &h->node_inst, ni), "ib") &&
+             ck(upload(h, &h->ibX, L.ib_X0), "ib") && ck(upload(h, &h->ibX0, L.ib_X0), "ib") &&
+             ck(upload(h, &h->ibVs, zero), "ib") && ck(upload(h, &h->ibI, zero), "ib") &&
+             ck(upload(h, &h->ibF, zero), "ib") && ck(upload(h, &h->ibVf, zero), "ib") &&
+             ck(upload(h, &h->ibdA, L.ib_dA), "ib") && ck(upload(h, &h->ibks, L.ib_ks), "ib") &&
+             ck(upload(h, &h->ibpin, L.ib_pinned), "ib") &&
+             ck(dalloc_bytes(h, &h->vband, 3 * n * h->rbytes), "vband");
+    }
+    if (!ok) {
+        lbm_status s = h->err.find("out of memory") != std::string::npos ? LBM_ERR_OOM : LBM_ERR_CUDA;
+        return bail(s, h->err);
+    }
+    h->kp.n = (long long)n;
+    h->kp.flags = h->flags;
+    h->kp.rows = h->rows;
+    h->kp.chunk_row = h->chunk_row;
+    h->kp.omega = h->omega;
+    h->kp.b = h->b;
+    h->kp.aux = h->aux;
+    h->kp.step = h->step_dev;
+    h->kp.status = h->status;
+    h->bp.n_bc_total = (int)L.bc.size();
+    h->bp.par = h->bc_par;
+    h->bp.state = h->bc_state;
+    h->bp.xf = h->xf;
+    h->bp.lk_xb = h->lk_xb;
+    h->bp.lk_xf = h->lk_xf;
+    h->bp.lk_node = h->lk_node;
+    h->bp.lk_xfi = h->lk_xfi;
+    h->bp.lk_i = h->lk_i;
+    h->bp.profile = h->profile;
+    h->bp.etab = h->etab;
+    h->bp.v0 = h->v0;
+    h->bp.wave = h->wave;
+    h->bp.wave_cap = h->wave_cap;
+    h->bp.partial = h->partial;
+    h->bp.n_red_blocks = (int)L.red_bc.size();
+    h->bp.n_app_blocks = (int)L.app_bc.size();
+    h->bp.red_bc = h->red_bc;
+    h->bp.red_chunk = h->red_chunk;
+    h->bp.app_bc = h->app_bc;
+    h->bp.app_chunk = h->app_chunk;
+    h->ibp.n_nodes = (int)ns;
+    h->ibp.n_band = (int)L.band.size();
+    h->ibp.band = h->band;
+    h->ibp.node_inst = h->node_inst;
+    h->ibp.inst = h->inst_dev;
+    h->ibp.rowid = h->rowid;
+    h->ibp.X = h->ibX;
+    h->ibp.Vs = h->ibVs;
+    h->ibp.I = h->ibI;
+    h->ibp.F = h->ibF;
+    h->ibp.Vf = h->ibVf;
+    h->ibp.X0 = h->ibX0;
+    h->ibp.dA = h->ibdA;
+    h->ibp.ks = h->ibks;
+    h->ibp.pinned = h->ibpin;
+    h->ibp.vband = h->vband;
+    if (cudaDeviceSynchronize() != cudaSuccess) return bail(LBM_ERR_CUDA, "set-up failed");
+    *out = h;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_0d_params(lbm_handle *h, int inst, int bc, const double *p, int np) {
+    if (bad_inst(h, inst)) return fail(h, LBM_ERR_ARG, "bad instance");
+    const InstParam &ip = h->L.inst[inst];
+    if (bc < 0 || bc >= ip.n_bc || !p || np < 1 || np > 8) return fail(h, LBM_ERR_ARG, "bad boundary or params");
+    BcParam &bp = h->L.bc[ip.bc_first + bc];
+    static const int need[4] = {1, 4, 4, 1};
+    if (np < need[bp.kind]) return fail(h, LBM_ERR_ARG, "too few params");
+    if (bp.kind == BC_RCR && (!(p[1] > 0) || !(p[2] > 0))) return fail(h, LBM_ERR_ARG, "RCR needs C, R_d > 0");
+    if (bp.kind == BC_LV && ((int)p[0] != bp.period || !(p[2] > 0)))
+        return fail(h, LBM_ERR_ARG, "LV period is fixed at creation; N_S > 0");
+    for (int k = 0; k < np; k++) bp.par[k] = p[k];
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(&h->bc_par[ip.bc_first + bc], &bp, sizeof(BcParam), cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
+lbm_status lbm_init_populations(lbm_handle *h, int inst, const double *f) {
+    if (bad_inst(h, inst) || !f) return fail(h, LBM_ERR_ARG, "bad instance or array");
+    CK(h, cudaSetDevice(h->device));
+    const Layout &L = h->L;
+    const int64_t c0 = L.inst_cell_begin[inst], c1 = L.inst_cell_end[inst];
+    const size_t M = (size_t)(c1 - c0);
+    const lbm_instance_desc &d = h->inst[inst];
+    const size_t nbox = (size_t)d.nx * d.ny * d.nz;
+    std::vector<double> host(NQ * M);
+    for (int i = 0; i < NQ; i++)
+        for (size_t k = 0; k < M; k++) host[i * M + k] = f[i * nbox + (size_t)L.cell_box[c0 + k]];
+    double *dev = nullptr;
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMalloc(&dev, host.size() * sizeof(double)));
+    cudaError_t e = cudaMemcpy(dev, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = launch_init(h->prec, h->f[h->parity], h->kp, dev, (int)c0, (int)c1, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    cudaFree(dev);
+    CK(h, e);
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_handle *h, int64_t n) {
+    if (!h || n < 0) return fail(h, LBM_ERR_ARG, "bad step count");
+    CK(h, cudaSetDevice(h->device));
+    if (h->timing) {
+        for (int64_t k = 0; k < n; k++) {
+            lbm_status s = launch_step(h, true);
+            if (s != LBM_OK) return s;
+            h->steps++;
+        }
+        return LBM_OK;
+    }
+    int64_t left = n;
+    while (left >= h->graph_steps) {
+        lbm_status s = ensure_graph(h);
+        if (s != LBM_OK) return s;
+        CK(h, cudaGraphLaunch(h->graph[h->parity], h->stream));
+        left -= h->graph_steps;
+        h->steps += h->graph_steps;
+    }
+    for (; left > 0; left--) {
+        lbm_status s = launch_step(h, false);
+        if (s != LBM_OK) return s;
+        h->steps++;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_handle *h) {
+    if (!h) return LBM_ERR_ARG;
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    unsigned s = 0;
+    CK(h, cudaMemcpy(&s, h->status, sizeof s, cudaMemcpyDeviceToHost));
+    if (s & 1u) return fail(h, LBM_ERR_UNSTABLE, "NaN/Inf or |v| > 0.3 in the lattice");
+    if (s & 2u) return fail(h, LBM_ERR_UNSTABLE, "a wall node moved outside its immersed-boundary band");
+    return LBM_OK;
+}
+
+lbm_status lbm_read_fields(lbm_handle *h, int inst, double *P, double *jx, double *jy, double *jz) {
+    if (bad_inst(h, inst) || !P || !jx || !jy || !jz) return fail(h, LBM_ERR_ARG, "bad instance or array");
+    CK(h, cudaSetDevice(h->device));
+    lbm_status s = read_gather(h);
+    if (s != LBM_OK) return s;
+    const Layout &L = h->L;
+    const int64_t c0 = L.inst_cell_begin[inst], c1 = L.inst_cell_end[inst];
+    const size_t M = (size_t)(c1 - c0), n = (size_t)L.n_stored;
+    std::vector<double> mac(4 * M);
+    for (int k = 0; k < 4; k++)
+        CK(h, cudaMemcpy(&mac[k * M], h->rd_mac + k * n + c0, M * sizeof(double), cudaMemcpyDeviceToHost));
+    const lbm_instance_desc &d = h->inst[inst];
+    const size_t nbox = (size_t)d.nx * d.ny * d.nz;
+    double *outs[4] = {P, jx, jy, jz};
+    for (int k = 0; k < 4; k++) {
+        std::fill(outs[k], outs[k] + nbox, 0.0);
+        for (size_t m = 0; m < M; m++) outs[k][L.cell_box[c0 + m]] = mac[k * M + m];
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_read_populations(lbm_handle *h, int inst, double *f) {
+    if (bad_inst(h, inst) || !f) return fail(h, LBM_ERR_ARG, "bad instance or array");
+    CK(h, cudaSetDevice(h->device));
+    lbm_status s = read_gather(h);
+    if (s != LBM_OK) return s;
+    const Layout &L = h->L;
+    const int64_t c0 = L.inst_cell_begin[inst], c1 = L.inst_cell_end[inst];
+    const size_t M = (size_t)(c1 - c0), n = (size_t)L.n_stored;
+    const lbm_instance_desc &d = h->inst[inst];
+    const size_t nbox = (size_t)d.nx * d.ny * d.nz;
+    std::vector<double> tmp(M);
+    for (int i = 0; i < NQ; i++) {
+        CK(h, cudaMemcpy(tmp.data(), h->rd_f19 + i * n + c0, M * sizeof(double), cudaMemcpyDeviceToHost));
+        double *o = f + i * nbox;
+        std::fill(o, o + nbox, 0.0);
+        for (size_t m = 0; m < M; m++) o[L.cell_box[c0 + m]] = tmp[m];
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_read_0d_state(lbm_handle *h, int inst, int bc, double *out) {
+    if (bad_inst(h, inst) || !out) return fail(h, LBM_ERR_ARG, "bad instance or array");
+    const InstParam &ip = h->L.inst[inst];
+    if (bc < 0 || bc >= ip.n_bc) return fail(h, LBM_ERR_ARG, "bad boundary");
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    BcState s;
+    const size_t slot = (size_t)(h->steps & 1) * h->L.bc.size() + ip.bc_first + bc;  // state of t_steps
+    CK(h, cudaMemcpy(&s, h->bc_state + slot, sizeof s, cudaMemcpyDeviceToHost));
+    const BcParam &bp = h->L.bc[ip.bc_first + bc];
+    out[0] = (double)h->steps;
+    out[1] = s.Q;
+    out[2] = s.Qu;
+    out[3] = s.Pbar - 1.0 / 3.0;
+    out[4] = bp.kind == BC_RCR ? s.Pw : (bp.kind == BC_LV ? s.Pv : s.Pstar_gauge);
+    out[5] = 0.0;
+    if (bp.kind == BC_LV) out[5] = s.Pv / h->L.etab[2 * (bp.etab_off + (int)(h->steps % bp.period))];
+    out[6] = s.valve_open;
+    out[7] = s.Td;
+    return LBM_OK;
+}
+
+lbm_status lbm_read_waveforms(lbm_handle *h, int inst, double *out, int64_t max_rows, int64_t *rows) {
+    if (bad_inst(h, inst) || !out || !rows || max_rows < 0) return fail(h, LBM_ERR_ARG, "bad arguments");
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    const InstParam &ip = h->L.inst[inst];
+    const int nb = (int)h->L.bc.size();
+    const int64_t have = std::min<int64_t>({h->steps, (int64_t)h->wave_cap, max_rows});
+    *rows = have;
+    if (have == 0) return LBM_OK;
+    std::vector<double> all((size_t)h->wave_cap * std::max(nb, 1) * 4, 0.0);
+    if (nb > 0) CK(h, cudaMemcpy(all.data(), h->wave, all.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    const int width = 1 + 4 * ip.n_bc;
+    for (int64_t r = 0; r < have; r++) {
+        const int64_t stepno = h->steps - have + r;
+        const size_t slot = (size_t)(stepno % h->wave_cap);
+        double *row = out + r * width;
+        row[0] = (double)stepno;
+        for (int k = 0; k < ip.n_bc; k++)
+            for (int m = 0; m < 4; m++) row[1 + 4 * k + m] = all[(slot * nb + ip.bc_first + k) * 4 + m];
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_read_ib(lbm_handle *h, int inst, double *X, double *Vs, double *F, double *Vf) {
+    if (bad_inst(h, inst)) return fail(h, LBM_ERR_ARG, "bad instance");
+    const InstParam &ip = h->L.inst[inst];
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    double *src[4] = {h->ibX, h->ibVs, h->ibF, h->ibVf};
+    double *dst[4] = {X, Vs, F, Vf};
+    for (int k = 0; k < 4; k++)
+        if (dst[k] && ip.n_ib)
+            CK(h, cudaMemcpy(dst[k], src[k] + 3 * (size_t)ip.ib_off, 3 * (size_t)ip.n_ib * sizeof(double),
+                             cudaMemcpyDeviceToHost));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_ib_state(lbm_handle *h, int inst, const double *X, const double *Vs) {
+    if (bad_inst(h, inst) || !X || !Vs) return fail(h, LBM_ERR_ARG, "bad arguments");
+    const InstParam &ip = h->L.inst[inst];
+    for (int64_t s = 0; s < 3LL * ip.n_ib; s++)
+        if (!std::isfinite(X[s]) || !std::isfinite(Vs[s])) return fail(h, LBM_ERR_ARG, "non-finite wall state");
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (ip.n_ib) {
+        CK(h, cudaMemcpy(h->ibX + 3 * (size_t)ip.ib_off, X, 3 * (size_t)ip.n_ib * sizeof(double), cudaMemcpyHostToDevice));
+        CK(h, cudaMemcpy(h->ibVs + 3 * (size_t)ip.ib_off, Vs, 3 * (size_t)ip.n_ib * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_kernel_timing(lbm_handle *h, int enable) {
+    if (!h) return LBM_ERR_ARG;
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (enable && h->ev.empty()) {
+        h->ev.resize(2048);
+        for (auto &e : h->ev) CK(h, cudaEventCreate(&e));
+    }
+    h->timing = enable != 0;
+    h->ev_used = 0;
+    h->timed_launches = 0;
+    h->timed_ms = 0.0;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_kernel_time(lbm_handle *h, int64_t *launches, double *total_ms) {
+    if (!h || !launches || !total_ms) return fail(h, LBM_ERR_ARG, "bad arguments");
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (size_t k = 0; k + 1 < h->ev_used; k += 2) {
+        float ms = 0.f;
+        CK(h, cudaEventElapsedTime(&ms, h->ev[k], h->ev[k + 1]));
+        h->timed_ms += ms;
+    }
+    h->ev_used = 0;
+    *launches = h->timed_launches;
+    *total_ms = h->timed_ms;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_info(lbm_handle *h, lbm_info_t *info) {
+    if (!h || !info) return LBM_ERR_ARG;
+    info->fluid_cells = h->L.n_fluid;
+    info->stored_cells = h->L.n_stored;
+    info->box_cells = h->L.n_box;
+    info->band_cells = (int64_t)h->L.band.size();
+    info->ib_nodes = (int64_t)h->L.ib_dA.size();
+    info->links = (int64_t)h->L.lk_xb.size();
+    info->steps = h->steps;
+    info->device_bytes = h->bytes;
+    info->precision = h->prec;
+    info->bytes_per_population = h->sbytes;
+    return LBM_OK;
+}
+
+const char *lbm_last_error(const lbm_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+void lbm_destroy(lbm_handle *h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    for (int k = 0; k < 2; k++)
+        if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+    for (auto e : h->ev) cudaEventDestroy(e);
+    for (void *p : h->allocs) cudaFree(p);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+}  // extern "C"

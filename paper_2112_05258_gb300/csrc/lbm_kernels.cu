@@ -1,0 +1,442 @@
+// Device kernels of the per-step hot path:
+//   k_stream_collide  fused pull-stream + halfway bounce-back + moments + BGK
+//                     collision with forcing (Eqs. fi, feq, f, rho, v), one
+//                     thread per stored cell of the compact row layout
+//   k_bc_reduce       deterministic FP64 partial sums of the boundary flow Q
+//                     and pressure over the first fluid layer of each 0D boundary
+//   k_bc_apply        the FP64 forward-Euler 0D step (Eqs. rightbc, rightQ,
+//                     LVE; valve switch and smoothing of Section 2.2.1) and
+//                     the ghost populations of Eq. Non-equilibrium3
+//   k_gather          read-out of f(t_n), P and j for the host
+//   k_init            inverse of the pull: lays out a given f(t_0)
+//
+// Populations are stored as deviations s_i = f_i - w_i (FP32, FP16, BF16 or
+// FP64) in structure-of-arrays order f[i][cell].  The resident state between
+// steps is the post-collision field f*(t_n) with the ghost populations of
+// the 0D boundary nodes for t_{n+1} already in their slots, so one step is:
+// (immersed boundary) -> k_stream_collide -> k_bc_reduce -> k_bc_apply.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "lbm_kernels.h"
+
+namespace lbm {
+
+template <class S> struct Storage;
+template <> struct Storage<float> {
+    using R = float;
+    static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
+};
+template <> struct Storage<double> {
+    using R = double;
+    static __device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(double *p, double v) { *p = v; }
+};
+template <> struct Storage<__half> {
+    using R = float;
+    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct Storage<__nv_bfloat16> {
+    using R = float;
+    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+__constant__ signed char c_ex[NQ] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+__constant__ signed char c_ey[NQ] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+__constant__ signed char c_ez[NQ] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+
+// row of compact cell c: start from the row of its 32-cell chunk and walk on
+__device__ __forceinline__ int find_row(const KParams &p, int c) {
+    int r = __ldg(&p.chunk_row[c >> 5]);
+    while (__ldg(&p.rows[r + 1].off) <= c) r++;
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Fused stream-collide.  For each fluid cell x and direction i the pulled
+// population is f*_i(x - e_i) (or f*_opp(i)(x) when x - e_i is a rigid wall:
+// halfway bounce-back).  Then P = c_s^2 sum f, j = sum e f, v = j + b/2
+// (Eqs. rho, v), f^eq (Eq. feq), the forcing F_i (Eq. f) and BGK relaxation
+// (Eq. fi).  With s = f - w: sum f = 1 + sum s, j = sum e s, and
+// f^eq_i - w_i = w_i (sum s + 3 e.v + 9/2 (e.v)^2 - 3/2 v^2).
+template <class S>
+__global__ void __launch_bounds__(256) k_stream_collide(const S *__restrict__ fin, S *__restrict__ fout,
+                                                        KParams p) {
+    using R = typename Storage<S>::R;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c == 0) *p.step += 1;  // the step index t_n seen by the boundary kernels
+    if (c >= p.n) return;
+    const uint32_t fl = __ldg(&p.flags[c]);
+    if (!(fl & FL_ACTIVE)) return;
+    const size_t N = (size_t)p.n;
+    const int r = find_row(p, c);
+    const int x = __ldg(&p.rows[r].x0) + (c - __ldg(&p.rows[r].off));
+    const int *nb = p.rows[r].nb;
+
+    R f[NQ];
+#pragma unroll
+    for (int i = 0; i < NQ; i++) {
+        size_t idx;
+        if (i == 0) {
+            idx = (size_t)c;
+        } else if (fl & (1u << i)) {
+            idx = (size_t)opp(i) * N + c;
+        } else {
+            idx = (size_t)i * N + (size_t)(__ldg(&nb[nbk(i)]) + x - cx(i));
+        }
+        f[i] = Storage<S>::ld(fin + idx);
+    }
+    R sd = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < NQ; i++) {
+        sd += f[i];
+        if (cx(i)) jx += cx(i) * f[i];
+        if (cy(i)) jy += cy(i) * f[i];
+        if (cz(i)) jz += cz(i) * f[i];
+    }
+    R bx = 0, by = 0, bz = 0;
+    const bool band = (fl & FL_BAND) != 0;
+    const R *b = static_cast<const R *>(p.b);
+    if (band) {
+        bx = b[c];
+        by = b[N + c];
+        bz = b[2 * N + c];
+    }
+    const R vx = jx + R(0.5) * bx, vy = jy + R(0.5) * by, vz = jz + R(0.5) * bz;
+    if (fl & FL_XF) {
+        R *aux = static_cast<R *>(p.aux);
+        aux[c] = sd;
+        aux[N + c] = jx;
+        aux[2 * N + c] = jy;
+        aux[3 * N + c] = jz;
+    }
+    const R vv = vx * vx + vy * vy + vz * vz;
+    if (!(sd - sd == R(0)) || !(vv <= R(0.09))) atomicOr(p.status, 1u);
+
+    const R omega = (R)__ldg(&p.omega[__ldg(&p.rows[r].inst)]);
+    const R usq = R(1.5) * vv;
+    const R kf = R(1) - R(0.5) * omega;
+#pragma unroll
+    for (int i = 0; i < NQ; i++) {
+        const R w = (R)wgt(i);
+        const R eu = R(cx(i)) * vx + R(cy(i)) * vy + R(cz(i)) * vz;
+        const R seq = w * (sd + R(3) * eu + R(4.5) * eu * eu - usq);
+        R post = f[i] - omega * (f[i] - seq);
+        if (band) {
+            const R eb = R(cx(i)) * bx + R(cy(i)) * by + R(cz(i)) * bz;
+            const R vb = vx * bx + vy * by + vz * bz;
+            post += kf * w * (R(3) * (eb - vb) + R(9) * eu * eb);
+        }
+        Storage<S>::st(fout + (size_t)i * N + c, post);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 0D coupling.  One CTA per boundary.
+__device__ __forceinline__ double smooth_to_zero(double t, double t0, double LS) {
+    // Eq. SmoothFunction
+    if (t < t0) return 1.0;
+    if (t > t0 + LS) return 0.0;
+    const double u = (t - t0) / LS;
+    if (u <= 0.0) return 1.0;
+    if (u >= 1.0) return 0.0;
+    return exp(2.0 * exp(-1.0 / u) / (u - 1.0));
+}
+
+template <class R>
+__device__ __forceinline__ void forced_velocity(const KParams &p, int cf, double v[3]) {
+    const size_t N = (size_t)p.n;
+    const R *aux = static_cast<const R *>(p.aux);
+    v[0] = (double)aux[N + cf];
+    v[1] = (double)aux[2 * N + cf];
+    v[2] = (double)aux[3 * N + cf];
+    if (__ldg(&p.flags[cf]) & FL_BAND) {
+        const R *b = static_cast<const R *>(p.b);
+        v[0] += 0.5 * (double)b[cf];
+        v[1] += 0.5 * (double)b[N + cf];
+        v[2] += 0.5 * (double)b[2 * N + cf];
+    }
+}
+
+// Partial sums of the boundary flow Q = sum n.j / sum f and of the pressure
+// over one chunk of a boundary's first fluid layer (FP64, fixed tree order).
+template <class R>
+__global__ void __launch_bounds__(BC_CHUNK) k_bc_reduce(KParams p, BcKParams q) {
+    const int b = q.red_bc[blockIdx.x], ch = q.red_chunk[blockIdx.x];
+    const BcParam &P = q.par[b];
+    const size_t N = (size_t)p.n;
+    const R *aux = static_cast<const R *>(p.aux);
+    const int a = ch * BC_CHUNK + threadIdx.x;
+    __shared__ double sQ[BC_CHUNK], sP[BC_CHUNK];
+    double Q = 0.0, Ps = 0.0;
+    if (a < P.n_xf) {
+        const int cf = q.xf[P.xf_off + a];
+        const double sf = 1.0 + (double)aux[cf];
+        Q = (double)P.sign * (double)aux[(size_t)(1 + P.axis) * N + cf] / sf;
+        Ps = sf / 3.0;
+    }
+    sQ[threadIdx.x] = Q;
+    sP[threadIdx.x] = Ps;
+    __syncthreads();
+    for (int s = BC_CHUNK / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sQ[threadIdx.x] += sQ[threadIdx.x + s];
+            sP[threadIdx.x] += sP[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        q.partial[2 * (P.red_off + ch)] = sQ[0];
+        q.partial[2 * (P.red_off + ch) + 1] = sP[0];
+    }
+}
+
+// The 0D step of one boundary from its state at t_n, given Q(t_n) and the
+// layer's pressure sum.  Returns the state at t_{n+1}.
+__device__ BcState zero_d_step(const BcParam &P, const BcState &old, double Qt, double Psum, long long n,
+                               const double *etab, int *ptype, int *closed, double *Smooth) {
+    const double PREF = 1.0 / 3.0;
+    BcState st = old;
+    st.Q = Qt;
+    st.Qu = P.q_scale ? Qt / (double)P.n_xf : Qt;
+    st.Pbar = Psum / (double)P.n_xf;
+    *ptype = 1;
+    *closed = 0;
+    *Smooth = 0.0;
+    if (P.kind == BC_RCR) {
+        // Eqs. rightbc/rightQ driven by the outflow -Q_u, forward Euler
+        const double Qout = -st.Qu;
+        const double Pw = old.Pw + (Qout / P.par[1] - old.Pw / (P.par[2] * P.par[1]));
+        st.Pw = Pw;
+        st.Pstar_gauge = Pw + P.par[0] * Qout;
+    } else if (P.kind == BC_PRESSURE) {
+        st.Pstar_gauge = P.par[0];
+    } else if (P.kind == BC_LV) {
+        // Eq. LVE with C_v = 1/E: P_v <- P_v - (1/C_v)(dC_v/dt P_v + Q), dC_v/dt = -E'/E^2
+        const int T = P.period;
+        const double E = etab[2 * (P.etab_off + (int)(n % T))];
+        const double Ed = etab[2 * (P.etab_off + (int)(n % T)) + 1];
+        const double Qin = (old.valve_open != 0.0) ? st.Qu : 0.0;
+        const double Cv = 1.0 / E, dCv = -Ed / (E * E);
+        double Pv = old.Pv - (1.0 / Cv) * (dCv * old.Pv + Qin);
+        if (old.valve_open != 0.0) {
+            if (st.Qu < 0.0) {  // closure: the inflow has reversed
+                st.valve_open = 0.0;
+                st.Td = (double)n;
+                *closed = 1;
+            }
+        } else {
+            if (Pv < P.par[1]) Pv = P.par[1];           // ideal mitral diode from P_la
+            if (Pv > st.Pbar - PREF) st.valve_open = 1.0;  // ventricle exceeds the inlet pressure
+        }
+        st.Pv = Pv;
+        st.Pstar_gauge = Pv;
+        *ptype = st.valve_open != 0.0;
+        *Smooth = smooth_to_zero((double)(n + 1), st.Td, P.par[2]);
+    } else {
+        *ptype = 0;
+    }
+    return st;
+}
+
+// Ghost populations of one chunk of links, Eq. Non-equilibrium3 written as
+//   f_i(x_b) = f*_i(x_f) + f^eq_i(P*, v*) - f^eq_i(P(x_f), v(x_f)),
+// since f*_i(x_f) = f^eq_i + (1 - 1/tau) f^neq_i + F_i at x_f.
+template <class S>
+__global__ void __launch_bounds__(BC_CHUNK) k_bc_apply(S *__restrict__ f, KParams p, BcKParams q) {
+    using R = typename Storage<S>::R;
+    const int b = q.app_bc[blockIdx.x], ch = q.app_chunk[blockIdx.x];
+    const BcParam &P = q.par[b];
+    const size_t N = (size_t)p.n;
+    const R *aux = static_cast<const R *>(p.aux);
+    const int tid = threadIdx.x;
+    const long long n = *p.step;
+    __shared__ double s_Pstar, s_S;
+    __shared__ int s_ptype, s_closed;
+    if (tid < 32) {
+        double Q = 0.0, Ps = 0.0;
+        for (int k = tid; k < P.n_red; k += 32) {
+            Q += q.partial[2 * (P.red_off + k)];
+            Ps += q.partial[2 * (P.red_off + k) + 1];
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            Q += __shfl_xor_sync(0xffffffffu, Q, o);
+            Ps += __shfl_xor_sync(0xffffffffu, Ps, o);
+        }
+        if (tid == 0) {
+            const BcState old = q.state[(size_t)(n & 1) * q.n_bc_total + b];
+            int ptype, closed;
+            double Sm;
+            const BcState st = zero_d_step(P, old, Q, Ps, n, q.etab, &ptype, &closed, &Sm);
+            if (ch == 0) {
+                q.state[(size_t)((n + 1) & 1) * q.n_bc_total + b] = st;
+                double *w = q.wave + ((size_t)(n % q.wave_cap) * q.n_bc_total + b) * 4;
+                w[0] = st.Qu;
+                w[1] = st.Pbar - 1.0 / 3.0;
+                w[2] = (P.kind == BC_RCR) ? st.Pw : (P.kind == BC_LV ? st.Pv : st.Pstar_gauge);
+                w[3] = st.valve_open;
+            }
+            s_ptype = ptype;
+            s_closed = closed;
+            s_S = Sm;
+            s_Pstar = 1.0 / 3.0 + st.Pstar_gauge;
+        }
+    }
+    __syncthreads();
+    const int L = ch * BC_CHUNK + tid;
+    if (L >= P.n_links) return;
+    const int cb = q.lk_xb[P.link_off + L];
+    const int cf = q.lk_xf[P.link_off + L];
+    const int i = q.lk_i[P.link_off + L];
+    const double Pf = (1.0 + (double)aux[cf]) / 3.0;
+    double vf[3];
+    forced_velocity<R>(p, cf, vf);
+    double Ps, vs[3];
+    if (s_ptype) {  // pressure-type: (P_0D(t_{n+1}), v(x_f, t_n))
+        Ps = s_Pstar;
+        vs[0] = vf[0];
+        vs[1] = vf[1];
+        vs[2] = vf[2];
+    } else {        // velocity-type: (P(x_f, t_n), v_0D(t_{n+1}))
+        Ps = Pf;
+        vs[0] = vs[1] = vs[2] = 0.0;
+        if (P.kind == BC_VELOCITY) {
+            const double *pr = q.profile + 3 * (size_t)(P.node_off + q.lk_node[P.link_off + L]);
+            const double wv = P.par[0], tn1 = (double)(n + 1);
+            vs[P.axis] = (double)P.sign * (pr[0] + pr[1] * cos(wv * tn1) - pr[2] * sin(wv * tn1));
+        } else if (P.kind == BC_LV) {  // closed valve: v_0(T_d) S(t, T_d, N_S)
+            double *v0 = q.v0 + 3 * (size_t)(P.xf_off + q.lk_xfi[P.link_off + L]);
+            double u0[3];
+            if (s_closed) {  // v_0(T_d) = v(x_f, T_d); links sharing x_f store the same value
+                u0[0] = v0[0] = vf[0];
+                u0[1] = v0[1] = vf[1];
+                u0[2] = v0[2] = vf[2];
+            } else {
+                u0[0] = v0[0];
+                u0[1] = v0[1];
+                u0[2] = v0[2];
+            }
+            vs[0] = u0[0] * s_S;
+            vs[1] = u0[1] * s_S;
+            vs[2] = u0[2] * s_S;
+        }
+    }
+    const double ex = c_ex[i], ey = c_ey[i], ez = c_ez[i];
+    const double w = i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+    const double eus = ex * vs[0] + ey * vs[1] + ez * vs[2];
+    const double euf = ex * vf[0] + ey * vf[1] + ez * vf[2];
+    const double us2 = vs[0] * vs[0] + vs[1] * vs[1] + vs[2] * vs[2];
+    const double uf2 = vf[0] * vf[0] + vf[1] * vf[1] + vf[2] * vf[2];
+    const double dfeq = w * 3.0 * (Ps - Pf) + w * (3.0 * (eus - euf) + 4.5 * (eus * eus - euf * euf) - 1.5 * (us2 - uf2));
+    const double post = (double)Storage<S>::ld(f + (size_t)i * N + cf);
+    Storage<S>::st(f + (size_t)i * N + cb, (R)(post + dfeq));
+}
+
+// ---------------------------------------------------------------------------
+// Read-out: f(t_n) = pull of the resident f*(t_{n-1}) (with ghosts), plus
+// P = c_s^2 sum f and j = sum e f, for every fluid cell.
+template <class S>
+__global__ void k_gather(const S *__restrict__ fin, KParams p, double *fout19, double *mac4) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= p.n) return;
+    const uint32_t fl = p.flags[c];
+    const size_t N = (size_t)p.n;
+    if (!(fl & FL_ACTIVE)) {
+        if (fout19)
+            for (int i = 0; i < NQ; i++) fout19[i * N + c] = 0.0;
+        for (int k = 0; k < 4; k++) mac4[k * N + c] = 0.0;
+        return;
+    }
+    const int r = find_row(p, c);
+    const int x = p.rows[r].x0 + (c - p.rows[r].off);
+    double s = 0, jx = 0, jy = 0, jz = 0;
+    for (int i = 0; i < NQ; i++) {
+        size_t idx;
+        if (i == 0) idx = c;
+        else if (fl & (1u << i)) idx = (size_t)opp(i) * N + c;
+        else idx = (size_t)i * N + (size_t)(p.rows[r].nb[nbk(i)] + x - cx(i));
+        const double fi = (double)Storage<S>::ld(fin + idx) + wgt(i);
+        if (fout19) fout19[i * N + c] = fi;
+        s += fi;
+        jx += cx(i) * fi;
+        jy += cy(i) * fi;
+        jz += cz(i) * fi;
+    }
+    mac4[c] = s / 3.0;
+    mac4[N + c] = jx;
+    mac4[2 * N + c] = jy;
+    mac4[3 * N + c] = jz;
+}
+
+// Inverse of the pull: given f(t_0) at the fluid cells of [c0, c1), write
+// every population into the slot it will be pulled from.
+template <class S>
+__global__ void k_init(S *__restrict__ fout, KParams p, const double *__restrict__ f19, int c0, int c1) {
+    const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= c1) return;
+    const uint32_t fl = p.flags[c];
+    if (!(fl & FL_ACTIVE)) return;
+    const size_t N = (size_t)p.n;
+    const size_t M = (size_t)(c1 - c0);
+    const int r = find_row(p, c);
+    const int x = p.rows[r].x0 + (c - p.rows[r].off);
+    for (int i = 0; i < NQ; i++) {
+        const double s = f19[i * M + (c - c0)] - wgt(i);
+        size_t idx;
+        if (i == 0) idx = c;
+        else if (fl & (1u << i)) idx = (size_t)opp(i) * N + c;
+        else idx = (size_t)i * N + (size_t)(p.rows[r].nb[nbk(i)] + x - cx(i));
+        Storage<S>::st(fout + idx, (typename Storage<S>::R)s);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+
+template <class S> static S *as(void *p) { return static_cast<S *>(p); }
+
+#define DISPATCH(prec, CALL)                                   \
+    switch (prec) {                                            \
+    case 0: { using S = float; CALL; } break;                  \
+    case 1: { using S = __half; CALL; } break;                 \
+    case 2: { using S = __nv_bfloat16; CALL; } break;          \
+    default: { using S = double; CALL; } break;                \
+    }
+
+cudaError_t launch_stream_collide(int prec, const void *fin, void *fout, const KParams &p, int block,
+                                  cudaStream_t s) {
+    const int grid = (int)((p.n + block - 1) / block);
+    DISPATCH(prec, (k_stream_collide<S><<<grid, block, 0, s>>>(static_cast<const S *>(fin), as<S>(fout), p)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_boundary(int prec, void *f, const KParams &p, const BcKParams &q, cudaStream_t s) {
+    if (q.n_bc_total == 0) return cudaSuccess;
+    if (prec == 3) k_bc_reduce<double><<<q.n_red_blocks, BC_CHUNK, 0, s>>>(p, q);
+    else k_bc_reduce<float><<<q.n_red_blocks, BC_CHUNK, 0, s>>>(p, q);
+    DISPATCH(prec, (k_bc_apply<S><<<q.n_app_blocks, BC_CHUNK, 0, s>>>(as<S>(f), p, q)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather(int prec, const void *fin, const KParams &p, double *f19, double *mac4,
+                          cudaStream_t s) {
+    const int block = 256;
+    const int grid = (int)((p.n + block - 1) / block);
+    DISPATCH(prec, (k_gather<S><<<grid, block, 0, s>>>(static_cast<const S *>(fin), p, f19, mac4)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init(int prec, void *fout, const KParams &p, const double *f19, int c0, int c1,
+                        cudaStream_t s) {
+    const int block = 256;
+    const int grid = (c1 - c0 + block - 1) / block;
+    if (grid == 0) return cudaSuccess;
+    DISPATCH(prec, (k_init<S><<<grid, block, 0, s>>>(as<S>(fout), p, f19, c0, c1)));
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

@@ -1,0 +1,69 @@
+// Kernel parameter blocks and launchers (internal to liblbm).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "lbm_internal.h"
+
+namespace lbm {
+
+// Lattice-wide pointers shared by the kernels (device memory).
+struct KParams {
+    long long n;                // stored cells = population stride
+    const uint32_t *flags;      // per cell
+    const RowInfo *rows;        // rows + sentinel
+    const int32_t *chunk_row;   // per 32-cell chunk
+    const double *omega;        // per instance, 1/tau
+    const void *b;              // force density, compute type, 3 x n
+    void *aux;                  // first-layer macros (sum s, jx, jy, jz), compute type, 4 x n
+    long long *step;            // index t_n of the step in progress
+    unsigned *status;           // bit 0: NaN/Inf or |v| > 0.3 seen
+};
+
+// 0D boundary tables (device memory).  The boundary work of a step runs as
+// two kernels: k_bc_reduce (one CTA per chunk of BC_CHUNK first-layer cells
+// writes an FP64 partial sum) and k_bc_apply (one CTA per chunk of BC_CHUNK
+// links: every CTA of a boundary sums the partials in the same fixed order,
+// evaluates the same 0D step from the state of t_n, and writes its ghosts;
+// the boundary's first CTA stores the state of t_{n+1}).
+struct BcKParams {
+    int n_bc_total;
+    const BcParam *par;
+    BcState *state;             // [2][n_bc_total]: step n reads state[n & 1], writes state[(n + 1) & 1]
+    const int32_t *xf;
+    const int32_t *lk_xb, *lk_xf, *lk_node, *lk_xfi;
+    const uint8_t *lk_i;
+    const double *profile;
+    const double *etab;
+    double *v0;                 // 3 per first-layer entry
+    double *wave;               // ring buffer [cap][n_bc_total][4]
+    int wave_cap;
+    double *partial;            // 2 per reduce chunk: sum n.j/sum f, sum P
+    int n_red_blocks, n_app_blocks;
+    const int32_t *red_bc, *red_chunk;  // per reduce block
+    const int32_t *app_bc, *app_chunk;  // per apply block
+};
+
+// Immersed-boundary tables (device memory).
+struct IbKParams {
+    int n_nodes;                // all instances
+    int n_band;
+    const int32_t *band;        // compact band cells
+    const int32_t *node_inst;   // per node
+    const InstParam *inst;
+    const int32_t *rowid;
+    double *X, *Vs, *I, *F, *Vf;  // 3 per node
+    const double *X0, *dA, *ks;
+    const uint8_t *pinned;
+    void *vband;                // unforced velocity at band cells, compute type, 3 x n
+};
+
+cudaError_t launch_stream_collide(int prec, const void *fin, void *fout, const KParams &p, int block,
+                                  cudaStream_t s);
+cudaError_t launch_boundary(int prec, void *f, const KParams &p, const BcKParams &q, cudaStream_t s);
+cudaError_t launch_gather(int prec, const void *fin, const KParams &p, double *f19, double *mac4,
+                          cudaStream_t s);
+cudaError_t launch_init(int prec, void *fout, const KParams &p, const double *f19, int c0, int c1,
+                        cudaStream_t s);
+cudaError_t launch_ib(int prec, const void *fin, const KParams &p, const IbKParams &ib, cudaStream_t s);
+
+}  // namespace lbm

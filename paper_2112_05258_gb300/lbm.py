@@ -1,0 +1,263 @@
+"""Python binding of liblbm (argument marshalling only).
+
+Every step of the method runs in the CUDA kernels behind ``include/lbm.h``;
+this module converts numpy arrays and instance descriptions into the C
+structures, calls the entry points of the same names, and raises on a
+non-zero status.  There is no fallback: if ``liblbm.so`` is missing or no
+GPU is present, creating a :class:`Lattice` fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(_HERE, "_build", "liblbm.so")
+
+F32, F16, BF16, F64 = 0, 1, 2, 3
+PRECISIONS = {"f32": F32, "fp32": F32, "f16": F16, "fp16": F16, "bf16": BF16, "f64": F64, "fp64": F64}
+STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA", -3: "LBM_ERR_OOM",
+          -4: "LBM_ERR_UNSTABLE", -5: "LBM_ERR_STATE"}
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+
+
+class BoundaryDesc(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("axis", ctypes.c_int), ("sign", ctypes.c_int),
+                ("n_params", ctypes.c_int), ("params", _dp),
+                ("n_profile", ctypes.c_int64), ("profile", _dp),
+                ("period", ctypes.c_int), ("elastance", _dp)]
+
+
+class InstanceDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("node", _u8p), ("tau", ctypes.c_double), ("q_scale", ctypes.c_int),
+                ("n_bc", ctypes.c_int), ("bc", ctypes.POINTER(BoundaryDesc)),
+                ("n_ib", ctypes.c_int64), ("ib_X0", _dp), ("ib_dA", _dp), ("ib_ks", _dp),
+                ("ib_pinned", _u8p), ("ib_alpha", ctypes.c_double), ("ib_beta", ctypes.c_double),
+                ("ib_ms", ctypes.c_double)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("n_instances", ctypes.c_int),
+                ("inst", ctypes.POINTER(InstanceDesc)), ("stream", ctypes.c_void_p),
+                ("device", ctypes.c_int), ("graph_steps", ctypes.c_int),
+                ("wave_capacity", ctypes.c_int), ("block_size", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("fluid_cells", ctypes.c_int64), ("stored_cells", ctypes.c_int64),
+                ("box_cells", ctypes.c_int64), ("band_cells", ctypes.c_int64),
+                ("ib_nodes", ctypes.c_int64), ("links", ctypes.c_int64), ("steps", ctypes.c_int64),
+                ("device_bytes", ctypes.c_int64), ("precision", ctypes.c_int),
+                ("bytes_per_population", ctypes.c_int)]
+
+
+EXPORTS = ["lbm_create", "lbm_set_0d_params", "lbm_init_populations", "lbm_step", "lbm_sync",
+           "lbm_read_fields", "lbm_read_populations", "lbm_read_0d_state", "lbm_read_waveforms",
+           "lbm_read_ib", "lbm_set_ib_state", "lbm_set_kernel_timing", "lbm_get_kernel_time",
+           "lbm_get_info", "lbm_last_error", "lbm_destroy"]
+
+_lib = None
+
+
+def load(path: str = SO_PATH):
+    """Loads liblbm.so (builds nothing; call ``build()`` first)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"liblbm.so not built at {path}; run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    H = ctypes.c_void_p
+    L.lbm_create.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(H)]
+    L.lbm_set_0d_params.argtypes = [H, ctypes.c_int, ctypes.c_int, _dp, ctypes.c_int]
+    L.lbm_init_populations.argtypes = [H, ctypes.c_int, _dp]
+    L.lbm_step.argtypes = [H, ctypes.c_int64]
+    L.lbm_sync.argtypes = [H]
+    L.lbm_read_fields.argtypes = [H, ctypes.c_int, _dp, _dp, _dp, _dp]
+    L.lbm_read_populations.argtypes = [H, ctypes.c_int, _dp]
+    L.lbm_read_0d_state.argtypes = [H, ctypes.c_int, ctypes.c_int, _dp]
+    L.lbm_read_waveforms.argtypes = [H, ctypes.c_int, _dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+    L.lbm_read_ib.argtypes = [H, ctypes.c_int, _dp, _dp, _dp, _dp]
+    L.lbm_set_ib_state.argtypes = [H, ctypes.c_int, _dp, _dp]
+    L.lbm_set_kernel_timing.argtypes = [H, ctypes.c_int]
+    L.lbm_get_kernel_time.argtypes = [H, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
+    L.lbm_get_info.argtypes = [H, ctypes.POINTER(Info)]
+    L.lbm_last_error.argtypes = [H]
+    L.lbm_last_error.restype = ctypes.c_char_p
+    L.lbm_destroy.argtypes = [H]
+    L.lbm_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("lbm_last_error", "lbm_destroy"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+class Lattice:
+    """A batch of lattice instances advanced together on one GPU.
+
+    ``instances``: objects with the attributes of :class:`workloads.Instance`
+    (``node``, ``tau``, ``boundaries``, ``ib``, ``q_scale``).
+    """
+
+    def __init__(self, instances: Sequence, precision="f32", device: int = 0,
+                 stream: Optional[int] = None, graph_steps: int = 0, wave_capacity: int = 0,
+                 block_size: int = 0):
+        L = load()
+        if isinstance(precision, str):
+            precision = PRECISIONS[precision.lower()]
+        self._keep = []
+        n = len(instances)
+        descs = (InstanceDesc * n)()
+        self.shapes = []
+        self.nbc = []
+        for q, inst in enumerate(instances):
+            nz, ny, nx = inst.node.shape
+            node = np.ascontiguousarray(inst.node, dtype=np.uint8).reshape(-1)
+            self._keep.append(node)
+            bcs = (BoundaryDesc * max(1, len(inst.boundaries)))()
+            for k, b in enumerate(inst.boundaries):
+                par = np.ascontiguousarray(b.params, dtype=np.float64)
+                self._keep.append(par)
+                bcs[k].kind, bcs[k].axis, bcs[k].sign = int(b.kind), int(b.axis), int(b.sign)
+                bcs[k].n_params, bcs[k].params = par.size, _p(par)
+                if b.profile is not None:
+                    prof = np.ascontiguousarray(b.profile, dtype=np.float64)
+                    self._keep.append(prof)
+                    bcs[k].n_profile, bcs[k].profile = prof.shape[0], _p(prof)
+                if b.elastance is not None:
+                    et = np.ascontiguousarray(b.elastance, dtype=np.float64)
+                    self._keep.append(et)
+                    bcs[k].period, bcs[k].elastance = et.shape[0], _p(et)
+            self._keep.append(bcs)
+            d = descs[q]
+            d.nx, d.ny, d.nz = nx, ny, nz
+            d.node = node.ctypes.data_as(_u8p)
+            d.tau = float(inst.tau)
+            d.q_scale = int(getattr(inst, "q_scale", 1))
+            d.n_bc = len(inst.boundaries)
+            d.bc = ctypes.cast(bcs, ctypes.POINTER(BoundaryDesc))
+            ib = getattr(inst, "ib", None)
+            if ib is not None and ib.n > 0:
+                arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (ib.X0, ib.dA, ib.ks)]
+                pin = np.ascontiguousarray(ib.pinned, dtype=np.uint8)
+                self._keep += arrs + [pin]
+                d.n_ib = ib.n
+                d.ib_X0, d.ib_dA, d.ib_ks = (_p(a) for a in arrs)
+                d.ib_pinned = pin.ctypes.data_as(_u8p)
+                d.ib_alpha, d.ib_beta, d.ib_ms = float(ib.alpha), float(ib.beta), float(ib.ms)
+            self.shapes.append((nx, ny, nz))
+            self.nbc.append(len(inst.boundaries))
+        cfg = Config(precision=int(precision), n_instances=n,
+                     inst=ctypes.cast(descs, ctypes.POINTER(InstanceDesc)),
+                     stream=ctypes.c_void_p(stream or 0), device=device, graph_steps=graph_steps,
+                     wave_capacity=wave_capacity, block_size=block_size)
+        h = ctypes.c_void_p()
+        st = L.lbm_create(ctypes.byref(cfg), ctypes.byref(h))
+        self._keep = None
+        if st != 0:
+            raise LBMError(st, "lbm_create failed (see stderr)")
+        self._h = h
+        self.precision = int(precision)
+        self.n_instances = n
+
+    def _ck(self, st):
+        if st != 0:
+            raise LBMError(st, load().lbm_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lbm_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # --- entry points ---------------------------------------------------
+    def set_0d_params(self, inst: int, bc: int, params):
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        self._ck(load().lbm_set_0d_params(self._h, inst, bc, _p(p), p.size))
+
+    def init_populations(self, inst: int, f: np.ndarray):
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        nx, ny, nz = self.shapes[inst]
+        if f.size != 19 * nx * ny * nz:
+            raise ValueError("populations must be 19 x nx*ny*nz")
+        self._ck(load().lbm_init_populations(self._h, inst, _p(f)))
+
+    def step(self, n: int = 1):
+        self._ck(load().lbm_step(self._h, int(n)))
+
+    def sync(self):
+        self._ck(load().lbm_sync(self._h))
+
+    def fields(self, inst: int = 0):
+        nx, ny, nz = self.shapes[inst]
+        out = [np.empty(nx * ny * nz) for _ in range(4)]
+        self._ck(load().lbm_read_fields(self._h, inst, *[_p(a) for a in out]))
+        return out
+
+    def populations(self, inst: int = 0) -> np.ndarray:
+        nx, ny, nz = self.shapes[inst]
+        out = np.empty((19, nx * ny * nz))
+        self._ck(load().lbm_read_populations(self._h, inst, _p(out)))
+        return out
+
+    def state_0d(self, inst: int, bc: int) -> np.ndarray:
+        out = np.empty(8)
+        self._ck(load().lbm_read_0d_state(self._h, inst, bc, _p(out)))
+        return out
+
+    def waves(self, inst: int = 0, max_rows: int = 1 << 30) -> np.ndarray:
+        info = self.info()
+        rows_cap = int(min(max_rows, info.steps, 1 << 24))
+        width = 1 + 4 * self.nbc[inst]
+        out = np.empty((max(rows_cap, 1), width))
+        rows = ctypes.c_int64()
+        self._ck(load().lbm_read_waveforms(self._h, inst, _p(out), rows_cap, ctypes.byref(rows)))
+        return out[:rows.value]
+
+    def ib_state(self, inst: int, n: int):
+        out = [np.empty((n, 3)) for _ in range(4)]
+        self._ck(load().lbm_read_ib(self._h, inst, *[_p(a) for a in out]))
+        return out  # X, Vs, F, Vf
+
+    def set_ib_state(self, inst: int, X, Vs):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        Vs = np.ascontiguousarray(Vs, dtype=np.float64)
+        self._ck(load().lbm_set_ib_state(self._h, inst, _p(X), _p(Vs)))
+
+    def set_kernel_timing(self, enable: bool):
+        self._ck(load().lbm_set_kernel_timing(self._h, int(bool(enable))))
+
+    def kernel_time(self):
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        self._ck(load().lbm_get_kernel_time(self._h, ctypes.byref(n), ctypes.byref(ms)))
+        return n.value, ms.value
+
+    def info(self) -> Info:
+        i = Info()
+        self._ck(load().lbm_get_info(self._h, ctypes.byref(i)))
+        return i

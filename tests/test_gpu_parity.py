@@ -1,0 +1,178 @@
+"""GPU path (liblbm through its C-ABI) against the CPU oracle on identical
+seeded inputs.
+
+* FP64 instantiation: populations, macroscopic fields, 0D states and
+  waveforms agree with the oracle to rounding (1e-12 absolute on f ~ 1/3,
+  i.e. ~1e-11 relative to the deviations), over several 32-cell chunks and
+  ragged row tails, for every boundary kind and the immersed boundary.
+* FP32 on the rigid-tube workload (24x24x64, Womersley inlet, RCR outlet):
+  pressure and flow waveforms within 1e-5 relative (max over time of the
+  difference over the waveform's peak) after 10^4 steps.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import Instance, configs, geometry
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Lattice():
+    from paper_2112_05258_gb300 import Lattice as L, load
+    load()
+    return L
+
+
+def run_gpu(Lattice, inst, steps, prec="f64", f0=None, **kw):
+    lat = Lattice([inst], precision=prec, **kw)
+    if f0 is not None:
+        lat.init_populations(0, f0)
+    lat.step(steps)
+    lat.sync()
+    return lat
+
+
+def run_oracle(inst, steps, f0=None):
+    o = oracle.Oracle(inst)
+    if f0 is not None:
+        o.set_populations(f0)
+    o.step(steps)
+    return o
+
+
+def assert_same(lat, o, inst, atol_f=1e-12, atol_w=1e-12):
+    fl = inst.node.reshape(-1) == 0
+    fg, fo = lat.populations(0), o.populations()
+    assert np.abs(fg[:, fl] - fo[:, fl]).max() < atol_f
+    mg, mo = lat.fields(0), o.macros()
+    for a, b in zip(mg, mo):
+        assert np.abs(a[fl] - b[fl]).max() < atol_f
+    wg, wo = lat.waves(0), o.waves()
+    assert wg.shape == wo.shape
+    assert np.array_equal(wg[:, 0], wo[:, 0])
+    if wg.shape[1] > 1:
+        assert np.abs(wg[:, 1:] - wo[:, 1:]).max() < atol_w
+    for k in range(len(inst.boundaries)):
+        sg, so = lat.state_0d(0, k), o.state_0d(k)
+        assert sg[0] == so[0] and sg[6] == so[6] and sg[7] == so[7]
+        assert np.allclose(sg[1:6], so[1:6], rtol=1e-10, atol=1e-14)
+
+
+def test_f64_closed_box_random(Lattice):
+    inst = Instance(node=geometry.closed_box(37, 11, 9), tau=0.7)   # rows of 35: ragged chunks
+    f0 = configs.random_populations(inst, seed=11, amp=1e-2)
+    lat = run_gpu(Lattice, inst, 150, f0=f0)
+    o = run_oracle(inst, 150, f0=f0)
+    assert_same(lat, o, inst)
+
+
+def test_f64_rigid_tube_womersley_rcr(Lattice):
+    inst = configs.rigid_tube(16, 16, 24, radius=5.0, period=200)
+    f0 = configs.random_populations(inst, seed=3, amp=1e-3)
+    lat = run_gpu(Lattice, inst, 300, f0=f0)
+    o = run_oracle(inst, 300, f0=f0)
+    assert_same(lat, o, inst)
+
+
+def test_f64_pressure_tube(Lattice):
+    inst = configs.pressure_tube(14, 14, 20, 4.5, 0.9, 2e-3, -1e-3)
+    lat = run_gpu(Lattice, inst, 200)
+    o = run_oracle(inst, 200)
+    assert_same(lat, o, inst)
+
+
+def test_f64_lv_hybrid_inlet(Lattice):
+    # several beats: the valve opens and closes, T_d and the smoothed closure
+    # velocity are exercised
+    inst = configs.lv_tube(period=600)
+    lat = run_gpu(Lattice, inst, 1500)
+    o = run_oracle(inst, 1500)
+    w = o.waves()
+    assert (np.diff(w[:, 4]) < 0).sum() >= 2        # at least two closures seen
+    assert_same(lat, o, inst, atol_f=1e-11, atol_w=1e-11)
+
+
+def test_f64_immersed_boundary(Lattice):
+    inst = configs.ib_tube()
+    lat = run_gpu(Lattice, inst, 300)
+    o = run_oracle(inst, 300)
+    assert_same(lat, o, inst)
+    n = inst.ib.n
+    for a, b in zip(lat.ib_state(0, n), o.ib_state()):
+        assert np.abs(a - b).max() < 1e-12
+
+
+def _wave_rel_err(wg, wo, nbc):
+    errs = {}
+    for k in range(nbc):
+        for col, name in ((1, "Q"), (2, "P")):
+            a, b = wg[:, 1 + 4 * k + col - 1], wo[:, 1 + 4 * k + col - 1]
+            errs[f"{name}{k}"] = np.abs(a - b).max() / np.abs(b).max()
+    return errs
+
+
+def test_f32_rigid_tube_1e4_steps(Lattice):
+    inst = configs.rigid_tube()      # 24x24x64, R = 8, tau = 0.8, Womersley 0.02, T = 1000, RCR
+    steps = 10000
+    lat = run_gpu(Lattice, inst, steps, prec="f32", wave_capacity=steps)
+    o = run_oracle(inst, steps)
+    errs = _wave_rel_err(lat.waves(0), o.waves(), 2)
+    assert max(errs.values()) < 1e-5, errs
+
+
+@pytest.mark.parametrize("prec,bound", [("f16", 5e-2), ("bf16", 2e-1)])
+def test_reduced_precision_waveform_error(Lattice, prec, bound):
+    inst = configs.rigid_tube()
+    steps = 2000
+    lat = run_gpu(Lattice, inst, steps, prec=prec)
+    o = run_oracle(inst, steps)
+    errs = _wave_rel_err(lat.waves(0), o.waves(), 2)
+    print(prec, errs)
+    assert max(errs.values()) < bound, errs
+
+
+def test_batch_equals_single(Lattice):
+    a = configs.rigid_tube(16, 16, 24, radius=5.0, period=200)
+    b = configs.lv_tube(period=600)
+    c = configs.ib_tube()
+    for prec in ("f32", "f64"):
+        batch = Lattice([a, b, c], precision=prec)
+        batch.step(400)
+        batch.sync()
+        for q, inst in enumerate((a, b, c)):
+            single = run_gpu(Lattice, inst, 400, prec=prec)
+            if inst.ib is None:      # same kernels, deterministic reductions: identical bits
+                assert np.array_equal(batch.populations(q), single.populations(0))
+                assert np.array_equal(batch.waves(q), single.waves(0))
+            else:                    # spreading uses atomics: equal to rounding
+                tol = 1e-6 if prec == "f32" else 1e-14
+                assert np.abs(batch.populations(q) - single.populations(0)).max() < tol
+                assert np.abs(batch.waves(q) - single.waves(0)).max() < tol
+
+
+def test_graph_equals_direct_launches(Lattice):
+    inst = configs.lv_tube(period=600)
+    g = Lattice([inst], precision="f32", graph_steps=8)
+    g.step(203)
+    d = Lattice([inst], precision="f32")
+    d.set_kernel_timing(True)
+    d.step(203)
+    n, ms = d.kernel_time()
+    assert n == 203 and ms > 0
+    assert np.array_equal(g.populations(0), d.populations(0))
+    assert np.array_equal(g.waves(0), d.waves(0))
+
+
+def test_unstable_state_is_reported(Lattice):
+    from paper_2112_05258_gb300 import LBMError
+    inst = Instance(node=geometry.closed_box(10, 10, 10), tau=0.52)
+    f0 = configs.random_populations(inst, seed=1, amp=0.0)
+    f0[1] += 0.4                     # a strong +x jet everywhere: |v| > 0.3
+    lat = Lattice([inst], precision="f32")
+    lat.init_populations(0, f0)
+    lat.step(5)
+    with pytest.raises(LBMError) as e:
+        lat.sync()
+    assert e.value.status == -4

@@ -109,3 +109,60 @@ def random_populations(inst: Instance, seed: int, amp: float = 1e-3) -> np.ndarr
     rng = np.random.default_rng(seed)
     pert = rng.uniform(-1.0, 1.0, size=(19, nx * ny * nz))
     return w[:, None] * (1.0 + amp * pert)
+
+
+def ib_ring_nodes(cx: float, cy: float, radius: float, z_centres, seed: int,
+                  k_nominal: float, alpha: float, beta: float, ms: float,
+                  pin_ends: bool = True):
+    """Lagrangian wall nodes on a cylinder of the given radius: one ring per
+    z in ``z_centres`` with round(2 pi R) nodes at unit arc spacing; area
+    weight = arc length x ring spacing; stiffness k_nominal x U[0.5, 2]
+    (seeded); the first and last ring pinned."""
+    from .spec import IBNodes
+    rng = np.random.default_rng(seed)
+    n_th = max(8, int(round(2 * np.pi * radius)))
+    th = 2 * np.pi * np.arange(n_th) / n_th
+    z_centres = np.asarray(z_centres, dtype=np.float64)
+    dz = float(z_centres[1] - z_centres[0]) if z_centres.size > 1 else 1.0
+    X = np.empty((z_centres.size * n_th, 3))
+    X[:, 0] = np.tile(cx + radius * np.cos(th), z_centres.size)
+    X[:, 1] = np.tile(cy + radius * np.sin(th), z_centres.size)
+    X[:, 2] = np.repeat(z_centres, n_th)
+    ns = X.shape[0]
+    dA = np.full(ns, 2 * np.pi * radius / n_th * dz)
+    ks = k_nominal * rng.uniform(0.5, 2.0, ns)
+    pinned = np.zeros(ns, np.uint8)
+    if pin_ends:
+        pinned[:n_th] = 1
+        pinned[-n_th:] = 1
+    return IBNodes(X0=X, dA=dA, ks=ks, pinned=pinned, alpha=alpha, beta=beta, ms=ms)
+
+
+# penalty gains and wall parameters of the elastic-wall workloads (lattice
+# units; the paper takes alpha, beta from earlier work without values)
+IB_ALPHA, IB_BETA, IB_MS, IB_K = -2.0e-3, -0.5, 1.0, 0.01
+
+
+def ib_tube(nx: int = 20, ny: int = 20, nz: int = 24, radius: float = 5.0,
+            margin: float = 3.0, tau: float = 0.8, u_peak: float = 0.01,
+            period: int = 400, seed: int = 0) -> Instance:
+    """Straight tube whose wall is a ring of Lagrangian nodes at ``radius``.
+
+    Fluid fills r < radius + margin so the kernel support of every wall node
+    lies in fluid; the 0D inlet (Womersley profile) and RCR outlet cover
+    r < radius only, the jacket outside the membrane is closed at both ends.
+    """
+    node = geometry.straight_tube(nx, ny, nz, radius + margin)
+    X, Y = np.meshgrid(np.arange(nx) + 0.5, np.arange(ny) + 0.5, indexing="xy")
+    outer = (X - nx / 2) ** 2 + (Y - ny / 2) ** 2 >= radius * radius
+    node[0][outer] = 1
+    node[nz - 1][outer] = 1
+    inst = Instance(node=node, tau=tau, name=f"ib_tube_{nx}x{ny}x{nz}_R{radius:g}")
+    omega = 2.0 * np.pi / period
+    r = geometry.node_radius(nx, ny, inst.boundary_nodes(0))
+    prof = profiles.womersley_coefficients(r, radius, omega, viscosity(tau), u_peak)
+    inst.boundaries.append(Boundary(BC_VELOCITY, 2, +1, [omega], profile=prof))
+    inst.boundaries.append(Boundary(BC_RCR, 2, -1, [0.05, 200.0, 1.0, 0.0]))
+    inst.ib = ib_ring_nodes(nx / 2, ny / 2, radius, np.arange(1, nz - 1) + 0.5, seed,
+                            IB_K, IB_ALPHA, IB_BETA, IB_MS)
+    return inst
