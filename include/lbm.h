@@ -176,6 +176,30 @@ lbm_status lbm_set_ib_state(lbm_handle *h, int inst, const double *X, const doub
 lbm_status lbm_set_kernel_timing(lbm_handle *h, int enable);
 lbm_status lbm_get_kernel_time(lbm_handle *h, int64_t *launches, double *total_ms);
 
+/* Stand-alone boundary flow and mean pressure over a caller-given list of
+ * lattice cells, for callers that cannot allocate device memory at the call
+ * (their device memory belongs to their own pool or framework allocator, or
+ * the call sits where cudaMalloc would synchronise or is not allowed).  The
+ * paper has no counterpart: it is the flux reduction that feeds the 0D
+ * models, offered without a handle and without allocation.
+ *   P, j_normal : device, indexed by the entries of cells; P is the lattice
+ *                 pressure c_s^2 sum_i f_i, j_normal = n . sum_i e_i f_i
+ *   cells       : device, n_cells indices into P and j_normal
+ *   out         : device, 2 doubles: {sum_k j_normal / (P / c_s^2), mean P}
+ *   stream      : cudaStream_t (NULL = legacy default stream)
+ * n_cells must lie in [1, 1048576]; larger requests return LBM_ERR_ARG with a
+ * message on stderr.  No memory is allocated: the FP64 partial sums live in
+ * a fixed 64 KiB device array that every GPU which loads the library holds
+ * until the process exits.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current, so make the
+ * first call on each device before any stream capture.  All calls share the
+ * array: each call overwrites every partial it reads, so no clearing is
+ * needed, but calls that overlap on the GPU (different streams, or
+ * concurrent host threads) race on it and must be serialised by the caller.
+ * The summation order is fixed, so results are deterministic. */
+lbm_status lbm_boundary_flux_noalloc(const double *P, const double *j_normal, const int32_t *cells,
+                                     int64_t n_cells, double *out, void *stream);
+
 lbm_status lbm_get_info(lbm_handle *h, lbm_info_t *info);
 const char *lbm_last_error(const lbm_handle *h);
 void lbm_destroy(lbm_handle *h);

@@ -60,7 +60,7 @@ class Info(ctypes.Structure):
 EXPORTS = ["lbm_create", "lbm_set_0d_params", "lbm_init_populations", "lbm_step", "lbm_sync",
            "lbm_read_fields", "lbm_read_populations", "lbm_read_0d_state", "lbm_read_waveforms",
            "lbm_read_ib", "lbm_set_ib_state", "lbm_set_kernel_timing", "lbm_get_kernel_time",
-           "lbm_get_info", "lbm_last_error", "lbm_destroy"]
+           "lbm_get_info", "lbm_last_error", "lbm_destroy", "lbm_boundary_flux_noalloc"]
 
 _lib = None
 
@@ -92,6 +92,8 @@ def load(path: str = SO_PATH):
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_destroy.argtypes = [H]
     L.lbm_destroy.restype = None
+    L.lbm_boundary_flux_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
     for name in EXPORTS:
         if name not in ("lbm_last_error", "lbm_destroy"):
             getattr(L, name).restype = ctypes.c_int
