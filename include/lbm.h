@@ -105,7 +105,7 @@ typedef struct {
     int device;        /* CUDA device ordinal */
     int graph_steps;   /* steps per captured CUDA graph (even, >= 2); 0 = 64 */
     int wave_capacity; /* waveform ring-buffer length in steps; 0 = 8192 */
-    int block_size;    /* threads per block of the stream-collide kernel, multiple of 32 in [32, 256]; 0 = 256 */
+    int block_size;    /* threads per block of the stream-collide kernel, multiple of 32 in [32, 256]; 0 = 128 */
 } lbm_config;
 
 typedef struct lbm_handle lbm_handle;

@@ -35,14 +35,16 @@ def _stale(obj: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra=None, out_dir: str = BUILD) -> str:
+    """Compiles into ``out_dir`` (default: the in-tree _build) and returns the .so path."""
+    os.makedirs(out_dir, exist_ok=True)
+    so = os.path.join(out_dir, "liblbm.so")
     inc = os.path.join(os.path.dirname(HERE), "include")
     hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(inc, "lbm.h"), __file__]
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(out_dir, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
             cmd = [nvcc()] + ARCH + FLAGS + (extra or []) + ["-I", inc, "-c", s, "-o", o]
@@ -59,13 +61,20 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         list(ex.map(run, jobs))
-    if jobs or force or _stale(SO, objs):
-        tmp = SO + f".{os.getpid()}.tmp"
+    if jobs or force or _stale(so, objs):
+        tmp = so + f".{os.getpid()}.tmp"
         run([nvcc()] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"])
-        os.replace(tmp, SO)
-    return SO
+        os.replace(tmp, so)
+    return so
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True,
-                extra=["-Xptxas", "-v"] if "--ptxas" in sys.argv else None))
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--force", action="store_true")
+    ap.add_argument("--ptxas", action="store_true", help="print register and spill counts")
+    ap.add_argument("--define", action="append", default=[], help="NAME=VALUE preprocessor definition")
+    ap.add_argument("--out", default=BUILD, help="output directory")
+    a = ap.parse_args()
+    extra = (["-Xptxas", "-v"] if a.ptxas else []) + [f"-D{d}" for d in a.define]
+    print(build(force=a.force, verbose=True, extra=extra, out_dir=os.path.abspath(a.out)))

@@ -233,7 +233,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
     static const int sb[4] = {4, 2, 2, 8};
     h->sbytes = sb[h->prec];
     h->rbytes = h->prec == LBM_F64 ? 8 : 4;
-    h->block = cfg->block_size ? cfg->block_size : 256;
+    h->block = cfg->block_size ? cfg->block_size : 128;
     h->graph_steps = cfg->graph_steps ? cfg->graph_steps : 64;
     h->wave_cap = cfg->wave_capacity > 0 ? cfg->wave_capacity : 8192;
     h->inst.assign(cfg->inst, cfg->inst + cfg->n_instances);
@@ -251,6 +251,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
     std::string e = build_layout(cfg, h->L);
     if (!e.empty()) return bail(LBM_ERR_ARG, e);
     Layout &L = h->L;
+    if ((double)NQ * (double)L.n_stored >= 2147483647.0)
+        return bail(LBM_ERR_ARG, "more than 2^31 / 19 stored cells (32-bit population offsets)");
     if (cudaSetDevice(h->device) != cudaSuccess) return bail(LBM_ERR_CUDA, "cudaSetDevice failed");
     if (cfg->stream) {
         h->stream = static_cast<cudaStream_t>(cfg->stream);
@@ -270,7 +272,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
         ok = ck(dalloc_bytes(h, &h->f[k], (size_t)NQ * n * h->sbytes), "populations");
         if (ok) ok = ck(cudaMemset(h->f[k], 0, (size_t)NQ * n * h->sbytes), "memset");
     }
-    if (ok) ok = ck(dalloc_bytes(h, &h->b, 3 * n * h->rbytes), "b") && ck(cudaMemset(h->b, 0, 3 * n * h->rbytes), "memset");
+    if (ok) ok = ck(dalloc_bytes(h, &h->b, 4 * n * h->rbytes), "b") && ck(cudaMemset(h->b, 0, 4 * n * h->rbytes), "memset");
     if (ok) ok = ck(dalloc_bytes(h, &h->aux, 4 * n * h->rbytes), "aux") && ck(cudaMemset(h->aux, 0, 4 * n * h->rbytes), "memset");
     if (ok) ok = ck(upload(h, &h->flags, L.flags), "flags");
     if (ok) ok = ck(upload(h, &h->rows, L.rows), "rows");
@@ -321,7 +323,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
              ck(upload(h, &h->ibF, zero), "ib") && ck(upload(h, &h->ibVf, zero), "ib") &&
              ck(upload(h, &h->ibdA, L.ib_dA), "ib") && ck(upload(h, &h->ibks, L.ib_ks), "ib") &&
              ck(upload(h, &h->ibpin, L.ib_pinned), "ib") &&
-             ck(dalloc_bytes(h, &h->vband, 3 * n * h->rbytes), "vband");
+             ck(dalloc_bytes(h, &h->vband, 4 * n * h->rbytes), "vband");
     }
     if (!ok) {
         lbm_status s = h->err.find("out of memory") != std::string::npos ? LBM_ERR_OOM : LBM_ERR_CUDA;

@@ -3,11 +3,13 @@
 // update (linear springs to the reference position, symplectic Euler).
 //
 //   k_band_moments  unforced velocity j/rho0 of f(t_n) at every band cell
-//                   (the cells within the support of a wall node) and b = 0
-//   k_ib_nodes      one thread per wall node: interpolate V_f with the 4-point
-//                   cosine delta, update the penalty integral and the force
-//                   F = alpha I + beta (V_f - V_s) on the fluid, spread
-//                   F delta dA into b, then move the node.
+//                   (the cells within reach of a wall node's kernel support)
+//                   and b = 0 there; both as one 4-vector per cell
+//   k_ib_nodes      one thread per wall node: gather V_f over the 64 support
+//                   cells of the 4-point cosine delta, penalty integral and
+//                   force F = alpha I + beta (V_f - V_s) on the fluid,
+//                   spreading of F delta dA with one vector atomic per cell,
+//                   spring update.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -28,6 +30,7 @@ template <> struct IbStorage<__nv_bfloat16> {
 template <class S>
 __global__ void k_band_moments(const S *__restrict__ fin, KParams p, IbKParams ib) {
     using R = typename IbStorage<S>::R;
+    using V = typename Vec4<R>::T;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ib.n_band) return;
     const int c = ib.band[t];
@@ -47,93 +50,138 @@ __global__ void k_band_moments(const S *__restrict__ fin, KParams p, IbKParams i
         if (cy(i)) jy += cy(i) * fi;
         if (cz(i)) jz += cz(i) * fi;
     }
-    R *v = static_cast<R *>(ib.vband);
-    v[c] = jx;
-    v[N + c] = jy;
-    v[2 * N + c] = jz;
-    R *b = static_cast<R *>(const_cast<void *>(p.b));
-    b[c] = 0;
-    b[N + c] = 0;
-    b[2 * N + c] = 0;
+    V v;
+    v.x = jx;
+    v.y = jy;
+    v.z = jz;
+    v.w = 0;
+    static_cast<V *>(ib.vband)[c] = v;
+    V z;
+    z.x = z.y = z.z = z.w = 0;
+    static_cast<V *>(const_cast<void *>(p.b))[c] = z;
 }
 
-// 4-point cosine discrete delta along one axis
-__device__ __forceinline__ double phi(double r) {
-    const double a = fabs(r);
-    if (a >= 2.0) return 0.0;
-    return 0.25 * (1.0 + cos(M_PI * r / 2.0));
+// Weights of the 4-point cosine delta phi(r) = (1 + cos(pi r / 2)) / 4 at the
+// offsets r_k = (k - 1) - th, k = 0..3, th in [0, 1): with C = cos(pi th / 2)
+// and S = sin(pi th / 2) they are (1 - S)/4, (1 + C)/4, (1 + S)/4, (1 - C)/4.
+template <class R> __device__ __forceinline__ R delta_weight(R Sn, R Cs, int k) {
+    const R v = (k == 0) ? -Sn : (k == 1) ? Cs : (k == 2) ? Sn : -Cs;
+    return R(0.25) * (R(1) + v);
+}
+__device__ __forceinline__ void sincospi_half(float th, float *s, float *c) { sincospif(0.5f * th, s, c); }
+__device__ __forceinline__ void sincospi_half(double th, double *s, double *c) { sincospi(0.5 * th, s, c); }
+
+__device__ __forceinline__ void vec_atomic_add(float4 *a, float4 v) { atomicAdd(a, v); }
+__device__ __forceinline__ void vec_atomic_add(double4a *a, double4a v) {
+    atomicAdd(&a->x, v.x);
+    atomicAdd(&a->y, v.y);
+    atomicAdd(&a->z, v.z);
 }
 
-template <class R> __device__ __forceinline__ void atomic_add(R *a, R v) { atomicAdd(a, v); }
-
+// One thread per wall node; a warp holds 32 consecutive nodes of a ring, so
+// at each support offset its atomics land on (mostly) different cells.  The
+// support is walked as 16 lattice lines (dy, dz) of 4 cells along x, with
+// one row lookup per line.
 template <class S>
-__global__ void k_ib_nodes(KParams p, IbKParams ib) {
+__global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib) {
     using R = typename IbStorage<S>::R;
+    using V = typename Vec4<R>::T;
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= ib.n_nodes) return;
-    const InstParam ip = ib.inst[ib.node_inst[s]];
-    const size_t N = (size_t)p.n;
-    double X[3], Vs[3];
+    const InstParam &ip = ib.inst[ib.node_inst[s]];
+    const int nx = ip.nx, ny = ip.ny, nz = ip.nz;
+    double X[3];
     int i0[3];
-    double ph[3][4];
+    R w[3][4];
+#pragma unroll
     for (int a = 0; a < 3; a++) {
         X[a] = ib.X[3 * s + a];
-        Vs[a] = ib.Vs[3 * s + a];
-        i0[a] = (int)floor(X[a] - 0.5);
-        for (int k = 0; k < 4; k++) ph[a][k] = phi((double)(i0[a] + k - 1) + 0.5 - X[a]);
+        const double h = X[a] - 0.5;
+        const double fl0 = floor(h);
+        i0[a] = (int)fl0;
+        R Sn, Cs;
+        sincospi_half((R)(h - fl0), &Sn, &Cs);
+#pragma unroll
+        for (int k = 0; k < 4; k++) w[a][k] = delta_weight<R>(Sn, Cs, k);
     }
-    const int dims[3] = {ip.nx, ip.ny, ip.nz};
-    int cell[64];
-    const R *vb = static_cast<const R *>(ib.vband);
-    double Vf[3] = {0.0, 0.0, 0.0};
+    const V *vb = static_cast<const V *>(ib.vband);
+    R vx = 0, vy = 0, vz = 0;
     bool out_of_band = false;
-    for (int dz = 0; dz < 4; dz++)
-        for (int dy = 0; dy < 4; dy++)
+#pragma unroll
+    for (int dz = 0; dz < 4; dz++) {
+        const int z = i0[2] + dz - 1;
+#pragma unroll
+        for (int dy = 0; dy < 4; dy++) {
+            const int y = i0[1] + dy - 1;
+            if (y < 0 || y >= ny || z < 0 || z >= nz) continue;
+            const int r = ib.rowid[ip.rowid_off + y + ny * z];
+            if (r < 0) continue;
+            const int x0 = p.rows[r].x0, len = p.rows[r].len, base = p.rows[r].off - x0;
+            const R wyz = w[1][dy] * w[2][dz];
+#pragma unroll
             for (int dx = 0; dx < 4; dx++) {
-                const int k = dx + 4 * (dy + 4 * dz);
-                cell[k] = -1;
-                const int x = i0[0] + dx - 1, y = i0[1] + dy - 1, z = i0[2] + dz - 1;
-                if (x < 0 || x >= dims[0] || y < 0 || y >= dims[1] || z < 0 || z >= dims[2]) continue;
-                const int r = ib.rowid[ip.rowid_off + y + ip.ny * z];
-                if (r < 0) continue;
-                const int x0 = p.rows[r].x0, len = p.rows[r].len;
+                const int x = i0[0] + dx - 1;
                 if (x < x0 || x >= x0 + len) continue;
-                const int c = p.rows[r].off + (x - x0);
+                const int c = base + x;
                 const uint32_t fl = p.flags[c];
-                if (!(fl & FL_ACTIVE)) continue;
+                if (!(fl & FL_ACTIVE)) continue;  // wall or boundary slot: no fluid, no force
                 if (!(fl & FL_BAND)) {
                     out_of_band = true;
                     continue;
                 }
-                cell[k] = c;
-                const double d = ph[0][dx] * ph[1][dy] * ph[2][dz];
-                Vf[0] += (double)vb[c] * d;
-                Vf[1] += (double)vb[N + c] * d;
-                Vf[2] += (double)vb[2 * N + c] * d;
+                const V v = vb[c];
+                const R d = w[0][dx] * wyz;
+                vx += v.x * d;
+                vy += v.y * d;
+                vz += v.z * d;
             }
+        }
+    }
     if (out_of_band) atomicOr(p.status, 2u);
-    double F[3];
+    const double Vf[3] = {(double)vx, (double)vy, (double)vz};
+    double F[3], Vs[3];
+#pragma unroll
     for (int a = 0; a < 3; a++) {
+        Vs[a] = ib.Vs[3 * s + a];
         const double dv = Vf[a] - Vs[a];
         const double I = ib.I[3 * s + a] + dv;
-        ib.I[3 * s + a] = I;
         F[a] = ip.alpha * I + ip.beta * dv;
+        ib.I[3 * s + a] = I;
         ib.F[3 * s + a] = F[a];
         ib.Vf[3 * s + a] = Vf[a];
     }
-    R *b = static_cast<R *>(const_cast<void *>(p.b));
-    const double dA = ib.dA[s];
-    for (int dz = 0; dz < 4; dz++)
-        for (int dy = 0; dy < 4; dy++)
+    const R dA = (R)ib.dA[s];
+    const R Fx = (R)F[0] * dA, Fy = (R)F[1] * dA, Fz = (R)F[2] * dA;
+    V *b = static_cast<V *>(const_cast<void *>(p.b));
+#pragma unroll
+    for (int dz = 0; dz < 4; dz++) {
+        const int z = i0[2] + dz - 1;
+#pragma unroll
+        for (int dy = 0; dy < 4; dy++) {
+            const int y = i0[1] + dy - 1;
+            if (y < 0 || y >= ny || z < 0 || z >= nz) continue;
+            const int r = ib.rowid[ip.rowid_off + y + ny * z];
+            if (r < 0) continue;
+            const int x0 = p.rows[r].x0, len = p.rows[r].len, base = p.rows[r].off - x0;
+            const R wyz = w[1][dy] * w[2][dz];
+#pragma unroll
             for (int dx = 0; dx < 4; dx++) {
-                const int c = cell[dx + 4 * (dy + 4 * dz)];
-                if (c < 0) continue;
-                const double d = ph[0][dx] * ph[1][dy] * ph[2][dz] * dA;
-                atomic_add<R>(&b[c], (R)(F[0] * d));
-                atomic_add<R>(&b[N + c], (R)(F[1] * d));
-                atomic_add<R>(&b[2 * N + c], (R)(F[2] * d));
+                const int x = i0[0] + dx - 1;
+                if (x < x0 || x >= x0 + len) continue;
+                const int c = base + x;
+                if ((p.flags[c] & (FL_ACTIVE | FL_BAND)) != (FL_ACTIVE | FL_BAND)) continue;
+                const R d = w[0][dx] * wyz;
+                V add;
+                add.x = Fx * d;
+                add.y = Fy * d;
+                add.z = Fz * d;
+                add.w = 0;
+                vec_atomic_add(&b[c], add);
             }
+        }
+    }
     if (!ib.pinned[s]) {
+#pragma unroll
         for (int a = 0; a < 3; a++) {
             const double acc = (-ib.ks[s] * (X[a] - ib.X0[3 * s + a]) - F[a]) / ip.ms;
             const double v = Vs[a] + acc;
@@ -147,23 +195,23 @@ cudaError_t launch_ib(int prec, const void *fin, const KParams &p, const IbKPara
     if (ib.n_nodes == 0) return cudaSuccess;
     const int block = 256;
     const int gb = (ib.n_band + block - 1) / block;
-    const int gn = (ib.n_nodes + block - 1) / block;
+    const int gn = (ib.n_nodes + 127) / 128;
     switch (prec) {
     case 0:
         if (gb) k_band_moments<float><<<gb, block, 0, st>>>(static_cast<const float *>(fin), p, ib);
-        k_ib_nodes<float><<<gn, block, 0, st>>>(p, ib);
+        k_ib_nodes<float><<<gn, 128, 0, st>>>(p, ib);
         break;
     case 1:
         if (gb) k_band_moments<__half><<<gb, block, 0, st>>>(static_cast<const __half *>(fin), p, ib);
-        k_ib_nodes<__half><<<gn, block, 0, st>>>(p, ib);
+        k_ib_nodes<__half><<<gn, 128, 0, st>>>(p, ib);
         break;
     case 2:
         if (gb) k_band_moments<__nv_bfloat16><<<gb, block, 0, st>>>(static_cast<const __nv_bfloat16 *>(fin), p, ib);
-        k_ib_nodes<__nv_bfloat16><<<gn, block, 0, st>>>(p, ib);
+        k_ib_nodes<__nv_bfloat16><<<gn, 128, 0, st>>>(p, ib);
         break;
     default:
         if (gb) k_band_moments<double><<<gb, block, 0, st>>>(static_cast<const double *>(fin), p, ib);
-        k_ib_nodes<double><<<gn, block, 0, st>>>(p, ib);
+        k_ib_nodes<double><<<gn, 128, 0, st>>>(p, ib);
         break;
     }
     return cudaGetLastError();

@@ -6,6 +6,13 @@
 
 namespace lbm {
 
+// Four-component vectors of the compute type, one per cell (array of structures),
+// so that a cell's force or velocity is one vector load and one vector atomic.
+template <class R> struct Vec4;
+template <> struct Vec4<float> { using T = float4; };
+struct alignas(32) double4a { double x, y, z, w; };
+template <> struct Vec4<double> { using T = double4a; };
+
 // Lattice-wide pointers shared by the kernels (device memory).
 struct KParams {
     long long n;                // stored cells = population stride
@@ -13,7 +20,7 @@ struct KParams {
     const RowInfo *rows;        // rows + sentinel
     const int32_t *chunk_row;   // per 32-cell chunk
     const double *omega;        // per instance, 1/tau
-    const void *b;              // force density, compute type, 3 x n
+    const void *b;              // force density b, 4 x compute type per cell (x, y, z, unused)
     void *aux;                  // first-layer macros (sum s, jx, jy, jz), compute type, 4 x n
     long long *step;            // index t_n of the step in progress
     unsigned *status;           // bit 0: NaN/Inf or |v| > 0.3 seen
@@ -54,7 +61,7 @@ struct IbKParams {
     double *X, *Vs, *I, *F, *Vf;  // 3 per node
     const double *X0, *dA, *ks;
     const uint8_t *pinned;
-    void *vband;                // unforced velocity at band cells, compute type, 3 x n
+    void *vband;                // unforced velocity at band cells, 4 x compute type per cell
 };
 
 cudaError_t launch_stream_collide(int prec, const void *fin, void *fout, const KParams &p, int block,

@@ -65,11 +65,13 @@ EXPORTS = ["lbm_create", "lbm_set_0d_params", "lbm_init_populations", "lbm_step"
 _lib = None
 
 
-def load(path: str = SO_PATH):
-    """Loads liblbm.so (builds nothing; call ``build()`` first)."""
+def load(path: Optional[str] = None):
+    """Loads liblbm.so (builds nothing; call ``build()`` first).  The
+    environment variable LBM_LIBRARY overrides the in-tree path."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or os.environ.get("LBM_LIBRARY") or SO_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"liblbm.so not built at {path}; run __graft_entry__.build()")
     L = ctypes.CDLL(path)
