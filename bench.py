@@ -36,7 +36,7 @@ sys.path.insert(0, ROOT)
 METRIC = "D3Q19 MLUPS & % HBM roofline; time-to-periodic-state vs plain FP32 at 1% error"
 FALLBACK_HBM_GBS = 6800.0
 BYTES_PER_CELL = {"f32": 152, "f16": 76, "bf16": 76, "f64": 304}
-PROFILE_MD = os.path.join(ROOT, "profiles", "stream_collide_aorta_f32.md")
+PROFILE_MD = os.path.join(ROOT, "profiles", "stream_collide_tube_f32.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_2112_05258_gb300", "csrc", "lbm_kernels.cu")
 
 
@@ -50,6 +50,9 @@ def parse_args():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--workload", choices=["aorta", "batch"], default="aorta",
+                    help="aorta: the full-size elastic-wall case (default); batch: 256 uneven rigid tubes")
+    ap.add_argument("--autotune", action="store_true", help="pick block size and occupancy variant first")
     return ap.parse_args()
 
 
@@ -58,12 +61,19 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def workload(seed):
+def workload(seed, kind="aorta"):
+    """Returns (instances, description)."""
+    if kind == "batch":
+        from workloads import batch
+        insts, _ = batch.tube_batch(256, seed)
+        desc = (f"batch of 256 rigid tubes, R in [6,20], L in [128,512], LV inlet + RCR outlet each, "
+                f"{sum(i.n_fluid for i in insts)} fluid cells, seed {seed}")
+        return insts, desc
     from workloads import aorta
     inst = aorta.build(seed)
     desc = (f"aorta {inst.shape[0]}x{inst.shape[1]}x{inst.shape[2]} tau={inst.tau} LV inlet + 3 RCR outlets, "
             f"{inst.ib.n} IB wall nodes, seed {seed}")
-    return inst, desc
+    return [inst], desc
 
 
 def measured_peaks():
@@ -129,6 +139,7 @@ class ClockSampler:
 
 
 def cpu_baseline(inst, seconds: float):
+    """Times the FP64 oracle on one instance for about ``seconds``."""
     import oracle
     o = oracle.Oracle(inst)
     t0 = time.perf_counter()
@@ -148,7 +159,8 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    inst, desc = workload(args.seed)
+    insts, desc = workload(args.seed, args.workload)
+    inst = insts[0]
     import oracle
     o = oracle.Oracle(inst)
     budget = 90.0
@@ -186,10 +198,15 @@ def main():
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     from paper_2112_05258_gb300 import Lattice
 
-    inst, desc = workload(args.seed)
+    insts, desc = workload(args.seed, args.workload)
+    inst = insts[0]
     stream = torch.cuda.Stream(device=local)
-    lat = Lattice([inst], precision=args.precision, device=local, stream=stream.cuda_stream)
+    wave_cap = 16384 if args.workload == "batch" else 0
+    lat = Lattice(insts, precision=args.precision, device=local, stream=stream.cuda_stream, wave_capacity=wave_cap)
     info = lat.info()
+    tuned = None
+    if args.autotune:
+        tuned = dict(zip(("block", "min_blocks_per_sm"), lat.autotune(iters=10)))
     cells = info.fluid_cells
     kernels_per_step = 3 + (2 if info.ib_nodes else 0)
 
@@ -232,7 +249,7 @@ def main():
     bytes_per_launch = BYTES_PER_CELL[args.precision] * cells
     achieved = bytes_per_launch / per_launch_s / 1e9
     peak, peak_src = measured_peaks()
-    traffic = profiled_traffic() if args.precision == "f32" else None
+    traffic = profiled_traffic() if (args.precision == "f32" and args.workload == "aorta") else None
 
     # end to end through the public API: every step the host writes the outlet
     # Windkessel parameters (H2D) and reads the 0D state of all boundaries (D2H)
@@ -254,7 +271,7 @@ def main():
            "steps": e2e_steps}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "aorta":
         cpu = cpu_baseline(inst, args.cpu_seconds)
 
     if rank == 0:
@@ -262,7 +279,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
                 "config": {"workload": desc, "fluid_cells": cells, "stored_cells": info.stored_cells,
-                           "ib_nodes": info.ib_nodes, "precision": args.precision,
+                           "ib_nodes": info.ib_nodes, "precision": args.precision, "autotuned": tuned,
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "l2": "inputs larger than L2 (no flush)"},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -168,6 +168,32 @@ lbm_status lbm_read_waveforms(lbm_handle *h, int inst, double *out, int64_t max_
 lbm_status lbm_read_ib(lbm_handle *h, int inst, double *X, double *Vs, double *F, double *Vf);
 lbm_status lbm_set_ib_state(lbm_handle *h, int inst, const double *X, const double *Vs);
 
+/* Sets f_i(x, t_0) = f^eq_i(P, v) (Eq. feq) at every fluid node of instance
+ * inst from host arrays of nx*ny*nz doubles (box order; non-fluid entries
+ * ignored, fluid entries must be finite): P is the lattice pressure (P_ref =
+ * 1/3 at rest), v the velocity.  Used to start from a predicted state. */
+lbm_status lbm_init_equilibrium(lbm_handle *h, int inst, const double *P, const double *vx, const double *vy,
+                                const double *vz);
+
+/* Overwrites the 0D state of boundary bc of instance inst with
+ * {P_w (RCR) or P_v (LV) gauge pressure, valve_open (0 or 1), T_d}. */
+lbm_status lbm_set_0d_state(lbm_handle *h, int inst, int bc, const double *state3);
+
+/* Cycle-to-cycle change of every instance's 0D waveforms: for instance q
+ * with period[q] steps, delta[q] = max over its boundaries and the waveforms
+ * Q_u and mean gauge pressure of max_t |W(t) - W(t - T)| / max_t |W(t - T)|
+ * over the last T = period[q] steps (host arrays of n_instances entries).
+ * delta[q] = -1 while fewer than 2 T steps have been taken; 2 T above the
+ * waveform capacity is LBM_ERR_ARG. */
+lbm_status lbm_cycle_change(lbm_handle *h, const int64_t *period, double *delta);
+
+/* Autotuner: times the stream-collide kernel for block sizes 64, 128, 192,
+ * 256 and three register/occupancy variants (at least 5, 6 or 8 resident
+ * 256-thread blocks per SM), `iters` launches each, on the handle's current
+ * state (which is left unchanged), and keeps the fastest.  Returns the chosen
+ * block size and minimum-blocks variant. */
+lbm_status lbm_autotune(lbm_handle *h, int iters, int *block, int *min_blocks);
+
 /* Kernel timing for roofline measurement.  While enabled, lbm_step launches
  * its kernels directly (no graph) and brackets every stream-collide launch
  * with CUDA events recorded on the handle's stream.  lbm_get_kernel_time

@@ -52,7 +52,12 @@ struct lbm_handle {
     double *ibX = nullptr, *ibVs = nullptr, *ibI = nullptr, *ibF = nullptr, *ibVf = nullptr;
     double *ibX0 = nullptr, *ibdA = nullptr, *ibks = nullptr;
     uint8_t *ibpin = nullptr;
-    double *rd_f19 = nullptr, *rd_mac = nullptr;  // read-out scratch (allocated on first read)
+    double *rd_f19 = nullptr, *rd_mac = nullptr;  // read-out scratch, largest instance (allocated on first use)
+    int64_t max_inst_cells = 0;
+    int variant = 0;  // stream-collide occupancy variant (see launch_stream_collide)
+    int *inst_bc = nullptr;  // per instance: bc_first, n_bc
+    long long *inst_period = nullptr;
+    double *inst_delta = nullptr;
     std::vector<void *> allocs;
     int64_t bytes = 0;
     KParams kp{};
@@ -174,7 +179,7 @@ lbm_status launch_step(lbm_handle *h, bool timed) {
         e1 = h->ev[h->ev_used++];
         CK(h, cudaEventRecord(e0, h->stream));
     }
-    CK(h, launch_stream_collide(h->prec, fin, fout, h->kp, h->block, h->stream));
+    CK(h, launch_stream_collide(h->prec, fin, fout, h->kp, h->block, h->variant, h->stream));
     if (timed) {
         CK(h, cudaEventRecord(e1, h->stream));
         h->timed_launches++;
@@ -204,13 +209,23 @@ lbm_status ensure_graph(lbm_handle *h) {
     return LBM_OK;
 }
 
-lbm_status read_gather(lbm_handle *h) {
-    const size_t n = (size_t)h->L.n_stored;
-    if (!h->rd_f19) CK(h, dalloc(h, &h->rd_f19, 19 * n));
-    if (!h->rd_mac) CK(h, dalloc(h, &h->rd_mac, 4 * n));
-    CK(h, launch_gather(h->prec, h->f[h->parity], h->kp, h->rd_f19, h->rd_mac, h->stream));
+lbm_status read_gather(lbm_handle *h, int inst, bool with_f) {
+    const size_t m = (size_t)h->max_inst_cells;
+    if (with_f && !h->rd_f19) CK(h, dalloc(h, &h->rd_f19, 19 * m));
+    if (!h->rd_mac) CK(h, dalloc(h, &h->rd_mac, 4 * m));
+    const int c0 = (int)h->L.inst_cell_begin[inst], c1 = (int)h->L.inst_cell_end[inst];
+    CK(h, launch_gather(h->prec, h->f[h->parity], h->kp, c0, c1, with_f ? h->rd_f19 : nullptr, h->rd_mac,
+                        h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;
+}
+
+void drop_graphs(lbm_handle *h) {
+    for (int k = 0; k < 2; k++)
+        if (h->graph[k]) {
+            cudaGraphExecDestroy(h->graph[k]);
+            h->graph[k] = nullptr;
+        }
 }
 
 bool bad_inst(lbm_handle *h, int inst) { return !h || inst < 0 || inst >= (int)h->inst.size(); }
@@ -324,6 +339,18 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
              ck(upload(h, &h->ibdA, L.ib_dA), "ib") && ck(upload(h, &h->ibks, L.ib_ks), "ib") &&
              ck(upload(h, &h->ibpin, L.ib_pinned), "ib") &&
              ck(dalloc_bytes(h, &h->vband, 4 * n * h->rbytes), "vband");
+    }
+    {
+        std::vector<int> ib2;
+        for (auto &ip : L.inst) {
+            ib2.push_back(ip.bc_first);
+            ib2.push_back(ip.n_bc);
+        }
+        for (size_t q = 0; q < L.inst.size(); q++)
+            h->max_inst_cells = std::max<int64_t>(h->max_inst_cells, L.inst_cell_end[q] - L.inst_cell_begin[q]);
+        if (ok) ok = ck(upload(h, &h->inst_bc, ib2), "instances") &&
+                     ck(dalloc(h, &h->inst_period, L.inst.size()), "instances") &&
+                     ck(dalloc(h, &h->inst_delta, L.inst.size()), "instances");
     }
     if (!ok) {
         lbm_status s = h->err.find("out of memory") != std::string::npos ? LBM_ERR_OOM : LBM_ERR_CUDA;
@@ -460,14 +487,13 @@ lbm_status lbm_sync(lbm_handle *h) {
 lbm_status lbm_read_fields(lbm_handle *h, int inst, double *P, double *jx, double *jy, double *jz) {
     if (bad_inst(h, inst) || !P || !jx || !jy || !jz) return fail(h, LBM_ERR_ARG, "bad instance or array");
     CK(h, cudaSetDevice(h->device));
-    lbm_status s = read_gather(h);
+    lbm_status s = read_gather(h, inst, false);
     if (s != LBM_OK) return s;
     const Layout &L = h->L;
     const int64_t c0 = L.inst_cell_begin[inst], c1 = L.inst_cell_end[inst];
-    const size_t M = (size_t)(c1 - c0), n = (size_t)L.n_stored;
+    const size_t M = (size_t)(c1 - c0);
     std::vector<double> mac(4 * M);
-    for (int k = 0; k < 4; k++)
-        CK(h, cudaMemcpy(&mac[k * M], h->rd_mac + k * n + c0, M * sizeof(double), cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(mac.data(), h->rd_mac, 4 * M * sizeof(double), cudaMemcpyDeviceToHost));
     const lbm_instance_desc &d = h->inst[inst];
     const size_t nbox = (size_t)d.nx * d.ny * d.nz;
     double *outs[4] = {P, jx, jy, jz};
@@ -481,16 +507,16 @@ lbm_status lbm_read_fields(lbm_handle *h, int inst, double *P, double *jx, doubl
 lbm_status lbm_read_populations(lbm_handle *h, int inst, double *f) {
     if (bad_inst(h, inst) || !f) return fail(h, LBM_ERR_ARG, "bad instance or array");
     CK(h, cudaSetDevice(h->device));
-    lbm_status s = read_gather(h);
+    lbm_status s = read_gather(h, inst, true);
     if (s != LBM_OK) return s;
     const Layout &L = h->L;
     const int64_t c0 = L.inst_cell_begin[inst], c1 = L.inst_cell_end[inst];
-    const size_t M = (size_t)(c1 - c0), n = (size_t)L.n_stored;
+    const size_t M = (size_t)(c1 - c0);
     const lbm_instance_desc &d = h->inst[inst];
     const size_t nbox = (size_t)d.nx * d.ny * d.nz;
     std::vector<double> tmp(M);
     for (int i = 0; i < NQ; i++) {
-        CK(h, cudaMemcpy(tmp.data(), h->rd_f19 + i * n + c0, M * sizeof(double), cudaMemcpyDeviceToHost));
+        CK(h, cudaMemcpy(tmp.data(), h->rd_f19 + i * M, M * sizeof(double), cudaMemcpyDeviceToHost));
         double *o = f + i * nbox;
         std::fill(o, o + nbox, 0.0);
         for (size_t m = 0; m < M; m++) o[L.cell_box[c0 + m]] = tmp[m];
@@ -598,6 +624,107 @@ lbm_status lbm_get_kernel_time(lbm_handle *h, int64_t *launches, double *total_m
     h->ev_used = 0;
     *launches = h->timed_launches;
     *total_ms = h->timed_ms;
+    return LBM_OK;
+}
+
+lbm_status lbm_init_equilibrium(lbm_handle *h, int inst, const double *P, const double *vx, const double *vy,
+                                const double *vz) {
+    if (bad_inst(h, inst) || !P || !vx || !vy || !vz) return fail(h, LBM_ERR_ARG, "bad instance or array");
+    CK(h, cudaSetDevice(h->device));
+    const Layout &L = h->L;
+    const int64_t c0 = L.inst_cell_begin[inst], c1 = L.inst_cell_end[inst];
+    const size_t M = (size_t)(c1 - c0);
+    const double *src[4] = {P, vx, vy, vz};
+    std::vector<double> host(4 * M);
+    for (int k = 0; k < 4; k++)
+        for (size_t m = 0; m < M; m++) {
+            const double v = src[k][(size_t)L.cell_box[c0 + m]];
+            if ((L.flags[c0 + m] & FL_ACTIVE) && !std::isfinite(v)) return fail(h, LBM_ERR_ARG, "non-finite field value");
+            host[k * M + m] = v;
+        }
+    if (!h->rd_mac) CK(h, dalloc(h, &h->rd_mac, 4 * (size_t)h->max_inst_cells));
+    CK(h, cudaStreamSynchronize(h->stream));
+    CK(h, cudaMemcpy(h->rd_mac, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CK(h, launch_init_eq(h->prec, h->f[h->parity], h->kp, h->rd_mac, (int)c0, (int)c1, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_set_0d_state(lbm_handle *h, int inst, int bc, const double *s3) {
+    if (bad_inst(h, inst) || !s3) return fail(h, LBM_ERR_ARG, "bad instance or array");
+    const InstParam &ip = h->L.inst[inst];
+    if (bc < 0 || bc >= ip.n_bc) return fail(h, LBM_ERR_ARG, "bad boundary");
+    if (!std::isfinite(s3[0]) || !(s3[1] == 0.0 || s3[1] == 1.0)) return fail(h, LBM_ERR_ARG, "bad 0D state");
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    const size_t slot = (size_t)(h->steps & 1) * h->L.bc.size() + ip.bc_first + bc;
+    BcState st;
+    CK(h, cudaMemcpy(&st, h->bc_state + slot, sizeof st, cudaMemcpyDeviceToHost));
+    const BcParam &bp = h->L.bc[ip.bc_first + bc];
+    if (bp.kind == BC_RCR) st.Pw = s3[0];
+    if (bp.kind == BC_LV) st.Pv = s3[0];
+    st.valve_open = s3[1];
+    st.Td = s3[2];
+    CK(h, cudaMemcpy(h->bc_state + slot, &st, sizeof st, cudaMemcpyHostToDevice));
+    return LBM_OK;
+}
+
+lbm_status lbm_cycle_change(lbm_handle *h, const int64_t *period, double *delta) {
+    if (!h || !period || !delta) return fail(h, LBM_ERR_ARG, "bad arguments");
+    const int ni = (int)h->inst.size();
+    std::vector<long long> per(ni);
+    for (int q = 0; q < ni; q++) {
+        if (period[q] < 1 || 2 * period[q] > h->wave_cap)
+            return fail(h, LBM_ERR_ARG, "period must be >= 1 and two periods must fit the waveform capacity");
+        per[q] = 2 * period[q] > h->steps ? 0 : period[q];  // 0: not enough history yet, delta = -1
+    }
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaMemcpyAsync(h->inst_period, per.data(), ni * sizeof(long long), cudaMemcpyHostToDevice, h->stream));
+    CK(h, launch_cycle_change(h->bp, h->inst_bc, h->inst_bc + 1, h->inst_period, (long long)h->steps, h->inst_delta, ni,
+                              h->stream));
+    CK(h, cudaMemcpyAsync(delta, h->inst_delta, ni * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_handle *h, int iters, int *block, int *min_blocks) {
+    if (!h || iters < 1 || !block || !min_blocks) return fail(h, LBM_ERR_ARG, "bad arguments");
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    KParams kp = h->kp;
+    kp.step = nullptr;  // timing launches must not advance the step index
+    void *fin = h->f[h->parity], *fout = h->f[1 - h->parity];
+    cudaEvent_t e0, e1;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    static const int blocks[4] = {64, 128, 192, 256};
+    float best = 1e30f;
+    int bb = h->block, bv = h->variant;
+    for (int v = 0; v < SC_VARIANTS; v++)
+        for (int bi = 0; bi < 4; bi++) {
+            CK(h, launch_stream_collide(h->prec, fin, fout, kp, blocks[bi], v, h->stream));  // warm-up
+            CK(h, cudaEventRecord(e0, h->stream));
+            for (int k = 0; k < iters; k++)
+                CK(h, launch_stream_collide(h->prec, fin, fout, kp, blocks[bi], v, h->stream));
+            CK(h, cudaEventRecord(e1, h->stream));
+            CK(h, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(h, cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                bb = blocks[bi];
+                bv = v;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the timing launches wrote f* from the resident state into the other buffer,
+    // which the next step overwrites; the resident state itself is unchanged
+    if (bb != h->block || bv != h->variant) drop_graphs(h);
+    h->block = bb;
+    h->variant = bv;
+    *block = bb;
+    *min_blocks = stream_collide_min_blocks(bv);
     return LBM_OK;
 }
 

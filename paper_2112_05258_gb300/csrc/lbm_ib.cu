@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= ib.n_nodes) return;
     const InstParam &ip = ib.inst[ib.node_inst[s]];
-    const int nx = ip.nx, ny = ip.ny, nz = ip.nz;
+    const int ny = ip.ny, nz = ip.nz;
     double X[3];
     int i0[3];
     R w[3][4];

@@ -8,7 +8,9 @@
 //                     LVE; valve switch and smoothing of Section 2.2.1) and
 //                     the ghost populations of Eq. Non-equilibrium3
 //   k_gather          read-out of f(t_n), P and j for the host
-//   k_init            inverse of the pull: lays out a given f(t_0)
+//   k_init, k_init_eq inverse of the pull: lays out a given f(t_0), or the
+//                     equilibrium of given macroscopic fields
+//   k_cycle_change    cycle-to-cycle change of the 0D waveforms
 //
 // Populations are stored as deviations s_i = f_i - w_i (FP32, FP16, BF16 or
 // FP64) in structure-of-arrays order f[i][cell].  The resident state between
@@ -63,19 +65,17 @@ __device__ __forceinline__ int find_row(const KParams &p, int c) {
 // (Eqs. rho, v), f^eq (Eq. feq), the forcing F_i (Eq. f) and BGK relaxation
 // (Eq. fi).  With s = f - w: sum f = 1 + sum s, j = sum e s, and
 // f^eq_i - w_i = w_i (sum s + 3 e.v + 9/2 (e.v)^2 - 3/2 v^2).
-// Occupancy request to ptxas: at least 6 resident 256-thread blocks per SM
-// caps the kernel at 40 registers (75 % occupancy) without spills; measured
-// on the aorta: 121 us per launch vs 131 us at 48 registers (5 blocks) and
-// 129 us at 32 registers (8 blocks, with spills).
-#ifndef LBM_SC_MIN_BLOCKS
-#define LBM_SC_MIN_BLOCKS 6
-#endif
-template <class S>
-__global__ void __launch_bounds__(256, LBM_SC_MIN_BLOCKS)
+// Occupancy request to ptxas (template parameter MINB: at least MINB resident
+// 256-thread blocks per SM).  MINB = 6 caps the kernel at 40 registers (75 %
+// occupancy) without spills; on the aorta it ran at 121 us per launch vs
+// 131 us at 48 registers (5 blocks) and 129 us at 32 registers (8 blocks,
+// with spills).  The variants are kept for the run-time autotuner.
+template <class S, int MINB>
+__global__ void __launch_bounds__(256, MINB)
     k_stream_collide(const S *__restrict__ fin, S *__restrict__ fout, KParams p) {
     using R = typename Storage<S>::R;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c == 0) *p.step += 1;  // the step index t_n seen by the boundary kernels
+    if (c == 0 && p.step) *p.step += 1;  // the step index t_n seen by the boundary kernels
     if (c >= p.n) return;
     const uint32_t fl = __ldg(&p.flags[c]);
     if (!(fl & FL_ACTIVE)) return;
@@ -342,38 +342,39 @@ __global__ void __launch_bounds__(BC_CHUNK) k_bc_apply(S *__restrict__ f, KParam
 
 // ---------------------------------------------------------------------------
 // Read-out: f(t_n) = pull of the resident f*(t_{n-1}) (with ghosts), plus
-// P = c_s^2 sum f and j = sum e f, for every fluid cell.
+// P = c_s^2 sum f and j = sum e f, for the cells [c0, c1) of one instance
+// (outputs indexed c - c0 with stride M = c1 - c0; non-fluid cells get 0).
 template <class S>
-__global__ void k_gather(const S *__restrict__ fin, KParams p, double *fout19, double *mac4) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= p.n) return;
+__global__ void k_gather(const S *__restrict__ fin, KParams p, int c0, int c1, double *fout19, double *mac4) {
+    const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= c1) return;
     const uint32_t fl = p.flags[c];
-    const size_t N = (size_t)p.n;
+    const size_t N = (size_t)p.n, M = (size_t)(c1 - c0), k = (size_t)(c - c0);
     if (!(fl & FL_ACTIVE)) {
         if (fout19)
-            for (int i = 0; i < NQ; i++) fout19[i * N + c] = 0.0;
-        for (int k = 0; k < 4; k++) mac4[k * N + c] = 0.0;
+            for (int i = 0; i < NQ; i++) fout19[i * M + k] = 0.0;
+        for (int a = 0; a < 4; a++) mac4[a * M + k] = 0.0;
         return;
     }
     const int r = find_row(p, c);
     const int x = p.rows[r].x0 + (c - p.rows[r].off);
-    double s = 0, jx = 0, jy = 0, jz = 0;
+    double sum = 0, jx = 0, jy = 0, jz = 0;
     for (int i = 0; i < NQ; i++) {
         size_t idx;
         if (i == 0) idx = c;
         else if (fl & (1u << i)) idx = (size_t)opp(i) * N + c;
         else idx = (size_t)i * N + (size_t)(p.rows[r].nb[nbk(i)] + x - cx(i));
         const double fi = (double)Storage<S>::ld(fin + idx) + wgt(i);
-        if (fout19) fout19[i * N + c] = fi;
-        s += fi;
+        if (fout19) fout19[i * M + k] = fi;
+        sum += fi;
         jx += cx(i) * fi;
         jy += cy(i) * fi;
         jz += cz(i) * fi;
     }
-    mac4[c] = s / 3.0;
-    mac4[N + c] = jx;
-    mac4[2 * N + c] = jy;
-    mac4[3 * N + c] = jz;
+    mac4[k] = sum / 3.0;
+    mac4[M + k] = jx;
+    mac4[2 * M + k] = jy;
+    mac4[3 * M + k] = jz;
 }
 
 // Inverse of the pull: given f(t_0) at the fluid cells of [c0, c1), write
@@ -398,6 +399,71 @@ __global__ void k_init(S *__restrict__ fout, KParams p, const double *__restrict
     }
 }
 
+// Equilibrium initialisation: f_i(x, t_0) = f^eq_i(P, v) (Eq. feq) from the
+// macroscopic fields of the fluid cells of [c0, c1) (4 x M doubles: P, vx,
+// vy, vz), laid out by the inverse of the pull like k_init.
+template <class S>
+__global__ void k_init_eq(S *__restrict__ fout, KParams p, const double *__restrict__ mac, int c0, int c1) {
+    const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= c1) return;
+    const uint32_t fl = p.flags[c];
+    if (!(fl & FL_ACTIVE)) return;
+    const size_t N = (size_t)p.n, M = (size_t)(c1 - c0), k = (size_t)(c - c0);
+    const double P = mac[k], vx = mac[M + k], vy = mac[2 * M + k], vz = mac[3 * M + k];
+    const double usq = 1.5 * (vx * vx + vy * vy + vz * vz);
+    const int r = find_row(p, c);
+    const int x = p.rows[r].x0 + (c - p.rows[r].off);
+    for (int i = 0; i < NQ; i++) {
+        const double eu = cx(i) * vx + cy(i) * vy + cz(i) * vz;
+        const double s = wgt(i) * (3.0 * P - 1.0 + 3.0 * eu + 4.5 * eu * eu - usq);  // f^eq_i - w_i
+        size_t idx;
+        if (i == 0) idx = c;
+        else if (fl & (1u << i)) idx = (size_t)opp(i) * N + c;
+        else idx = (size_t)i * N + (size_t)(p.rows[r].nb[nbk(i)] + x - cx(i));
+        Storage<S>::st(fout + idx, (typename Storage<S>::R)s);
+    }
+}
+
+// Cycle-to-cycle change of the boundary waveforms of one instance per CTA:
+// over the last `period` recorded steps t, max over waveforms W in {Q_u, mean
+// P} of each boundary of max_t |W(t) - W(t - period)| / max_t |W(t - period)|.
+__global__ void k_cycle_change(BcKParams q, const int *bc_first, const int *n_bc, const long long *period,
+                               long long steps, double *delta) {
+    const int inst = blockIdx.x;
+    const long long T = period[inst];
+    if (T <= 0) {
+        if (threadIdx.x == 0) delta[inst] = -1.0;
+        return;
+    }
+    __shared__ double s_num[256], s_den[256];
+    double worst = 0.0;
+    for (int k = 0; k < n_bc[inst]; k++) {
+        const int b = bc_first[inst] + k;
+        for (int wv = 0; wv < 2; wv++) {
+            double num = 0.0, den = 0.0;
+            for (long long t = steps - T + threadIdx.x; t < steps; t += blockDim.x) {
+                const double a = q.wave[((size_t)(t % q.wave_cap) * q.n_bc_total + b) * 4 + wv];
+                const double c = q.wave[((size_t)((t - T) % q.wave_cap) * q.n_bc_total + b) * 4 + wv];
+                num = fmax(num, fabs(a - c));
+                den = fmax(den, fabs(c));
+            }
+            s_num[threadIdx.x] = num;
+            s_den[threadIdx.x] = den;
+            __syncthreads();
+            for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+                if (threadIdx.x < s) {
+                    s_num[threadIdx.x] = fmax(s_num[threadIdx.x], s_num[threadIdx.x + s]);
+                    s_den[threadIdx.x] = fmax(s_den[threadIdx.x], s_den[threadIdx.x + s]);
+                }
+                __syncthreads();
+            }
+            if (s_den[0] > 0.0) worst = fmax(worst, s_num[0] / s_den[0]);
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) delta[inst] = worst;
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 
@@ -411,10 +477,22 @@ template <class S> static S *as(void *p) { return static_cast<S *>(p); }
     default: { using S = double; CALL; } break;                \
     }
 
+int stream_collide_min_blocks(int variant) { return variant == 1 ? 8 : (variant == 2 ? 5 : 6); }
+
 cudaError_t launch_stream_collide(int prec, const void *fin, void *fout, const KParams &p, int block,
-                                  cudaStream_t s) {
+                                  int variant, cudaStream_t s) {
     const int grid = (int)((p.n + block - 1) / block);
-    DISPATCH(prec, (k_stream_collide<S><<<grid, block, 0, s>>>(static_cast<const S *>(fin), as<S>(fout), p)));
+    switch (variant) {
+    case 1:
+        DISPATCH(prec, (k_stream_collide<S, 8><<<grid, block, 0, s>>>(static_cast<const S *>(fin), as<S>(fout), p)));
+        break;
+    case 2:
+        DISPATCH(prec, (k_stream_collide<S, 5><<<grid, block, 0, s>>>(static_cast<const S *>(fin), as<S>(fout), p)));
+        break;
+    default:
+        DISPATCH(prec, (k_stream_collide<S, 6><<<grid, block, 0, s>>>(static_cast<const S *>(fin), as<S>(fout), p)));
+        break;
+    }
     return cudaGetLastError();
 }
 
@@ -426,11 +504,27 @@ cudaError_t launch_boundary(int prec, void *f, const KParams &p, const BcKParams
     return cudaGetLastError();
 }
 
-cudaError_t launch_gather(int prec, const void *fin, const KParams &p, double *f19, double *mac4,
+cudaError_t launch_gather(int prec, const void *fin, const KParams &p, int c0, int c1, double *f19, double *mac4,
                           cudaStream_t s) {
     const int block = 256;
-    const int grid = (int)((p.n + block - 1) / block);
-    DISPATCH(prec, (k_gather<S><<<grid, block, 0, s>>>(static_cast<const S *>(fin), p, f19, mac4)));
+    const int grid = (c1 - c0 + block - 1) / block;
+    if (grid == 0) return cudaSuccess;
+    DISPATCH(prec, (k_gather<S><<<grid, block, 0, s>>>(static_cast<const S *>(fin), p, c0, c1, f19, mac4)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_eq(int prec, void *fout, const KParams &p, const double *mac, int c0, int c1,
+                           cudaStream_t s) {
+    const int block = 256;
+    const int grid = (c1 - c0 + block - 1) / block;
+    if (grid == 0) return cudaSuccess;
+    DISPATCH(prec, (k_init_eq<S><<<grid, block, 0, s>>>(as<S>(fout), p, mac, c0, c1)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cycle_change(const BcKParams &q, const int *bc_first, const int *n_bc, const long long *period,
+                                long long steps, double *delta, int n_inst, cudaStream_t s) {
+    k_cycle_change<<<n_inst, 256, 0, s>>>(q, bc_first, n_bc, period, steps, delta);
     return cudaGetLastError();
 }
 

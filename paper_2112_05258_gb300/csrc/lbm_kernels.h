@@ -64,11 +64,19 @@ struct IbKParams {
     void *vband;                // unforced velocity at band cells, 4 x compute type per cell
 };
 
+// variant: 0 = at least 6 blocks of 256 per SM (40 registers), 1 = 8 blocks
+// (32 registers), 2 = 5 blocks (48 registers)
+constexpr int SC_VARIANTS = 3;
+int stream_collide_min_blocks(int variant);
 cudaError_t launch_stream_collide(int prec, const void *fin, void *fout, const KParams &p, int block,
-                                  cudaStream_t s);
+                                  int variant, cudaStream_t s);
 cudaError_t launch_boundary(int prec, void *f, const KParams &p, const BcKParams &q, cudaStream_t s);
-cudaError_t launch_gather(int prec, const void *fin, const KParams &p, double *f19, double *mac4,
+cudaError_t launch_gather(int prec, const void *fin, const KParams &p, int c0, int c1, double *f19, double *mac4,
                           cudaStream_t s);
+cudaError_t launch_init_eq(int prec, void *fout, const KParams &p, const double *mac, int c0, int c1,
+                           cudaStream_t s);
+cudaError_t launch_cycle_change(const BcKParams &q, const int *bc_first, const int *n_bc, const long long *period,
+                                long long steps, double *delta, int n_inst, cudaStream_t s);
 cudaError_t launch_init(int prec, void *fout, const KParams &p, const double *f19, int c0, int c1,
                         cudaStream_t s);
 cudaError_t launch_ib(int prec, const void *fin, const KParams &p, const IbKParams &ib, cudaStream_t s);

@@ -60,7 +60,8 @@ class Info(ctypes.Structure):
 EXPORTS = ["lbm_create", "lbm_set_0d_params", "lbm_init_populations", "lbm_step", "lbm_sync",
            "lbm_read_fields", "lbm_read_populations", "lbm_read_0d_state", "lbm_read_waveforms",
            "lbm_read_ib", "lbm_set_ib_state", "lbm_set_kernel_timing", "lbm_get_kernel_time",
-           "lbm_get_info", "lbm_last_error", "lbm_destroy", "lbm_boundary_flux_noalloc"]
+           "lbm_get_info", "lbm_last_error", "lbm_destroy", "lbm_boundary_flux_noalloc",
+           "lbm_init_equilibrium", "lbm_set_0d_state", "lbm_cycle_change", "lbm_autotune"]
 
 _lib = None
 
@@ -94,6 +95,10 @@ def load(path: Optional[str] = None):
     L.lbm_last_error.restype = ctypes.c_char_p
     L.lbm_destroy.argtypes = [H]
     L.lbm_destroy.restype = None
+    L.lbm_init_equilibrium.argtypes = [H, ctypes.c_int, _dp, _dp, _dp, _dp]
+    L.lbm_set_0d_state.argtypes = [H, ctypes.c_int, ctypes.c_int, _dp]
+    L.lbm_cycle_change.argtypes = [H, ctypes.POINTER(ctypes.c_int64), _dp]
+    L.lbm_autotune.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
     L.lbm_boundary_flux_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
     for name in EXPORTS:
@@ -260,6 +265,30 @@ class Lattice:
         ms = ctypes.c_double()
         self._ck(load().lbm_get_kernel_time(self._h, ctypes.byref(n), ctypes.byref(ms)))
         return n.value, ms.value
+
+    def init_equilibrium(self, inst: int, P, vx, vy, vz):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in (P, vx, vy, vz)]
+        nx, ny, nz = self.shapes[inst]
+        if any(a.size != nx * ny * nz for a in arrs):
+            raise ValueError("fields must have nx*ny*nz entries")
+        self._ck(load().lbm_init_equilibrium(self._h, inst, *[_p(a) for a in arrs]))
+
+    def set_0d_state(self, inst: int, bc: int, state, valve_open: float = 0.0, Td: float = -1e300):
+        s = np.array([float(state), float(valve_open), float(Td)])
+        self._ck(load().lbm_set_0d_state(self._h, inst, bc, _p(s)))
+
+    def cycle_change(self, periods) -> np.ndarray:
+        per = np.ascontiguousarray(periods, dtype=np.int64)
+        if per.size != self.n_instances:
+            raise ValueError("one period per instance")
+        out = np.empty(self.n_instances)
+        self._ck(load().lbm_cycle_change(self._h, per.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _p(out)))
+        return out
+
+    def autotune(self, iters: int = 20):
+        b, m = ctypes.c_int(), ctypes.c_int()
+        self._ck(load().lbm_autotune(self._h, int(iters), ctypes.byref(b), ctypes.byref(m)))
+        return b.value, m.value
 
     def info(self) -> Info:
         i = Info()

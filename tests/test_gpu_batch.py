@@ -1,0 +1,102 @@
+"""GPU tests of the batching, periodic-state and initialisation entry points."""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import batch, configs
+
+pytestmark = pytest.mark.gpu
+CS2 = 1.0 / 3.0
+
+
+@pytest.fixture(scope="module")
+def Lattice():
+    from paper_2112_05258_gb300 import Lattice as L, load
+    load()
+    return L
+
+
+def _fields(inst):
+    nx, ny, nz = inst.shape
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    r2 = (x + 0.5 - nx / 2) ** 2 + (y + 0.5 - ny / 2) ** 2
+    P = CS2 + 1e-3 * (1 - z / nz) + 2e-4 * np.sin(0.3 * x)
+    uz = 0.01 * np.clip(1 - r2 / 25.0, 0, None)
+    ux = 1e-3 * np.cos(0.2 * z)
+    uy = np.zeros_like(uz)
+    return [a.reshape(-1) for a in (P, ux, uy, uz)]
+
+
+def test_init_equilibrium_matches_oracle(Lattice):
+    inst = configs.rigid_tube(16, 16, 24, radius=5.0, period=200)
+    P, ux, uy, uz = _fields(inst)
+    lat = Lattice([inst], precision="f64")
+    lat.init_equilibrium(0, P, ux, uy, uz)
+    f0 = np.stack([oracle.feq(P[c], [ux[c], uy[c], uz[c]]) for c in range(P.size)], axis=1)
+    fl = inst.node.reshape(-1) == 0
+    assert np.abs(lat.populations(0)[:, fl] - f0[:, fl]).max() < 1e-15
+    o = oracle.Oracle(inst)
+    o.set_populations(f0)
+    lat.step(120)
+    o.step(120)
+    assert np.abs(lat.populations(0)[:, fl] - o.populations()[:, fl]).max() < 1e-12
+    assert np.abs(lat.waves(0)[:, 1:] - o.waves()[:, 1:]).max() < 1e-12
+
+
+def test_cycle_change_matches_waveforms(Lattice):
+    insts = [configs.lv_tube(period=600), configs.lv_tube(period=400)]
+    lat = Lattice(insts, precision="f32", wave_capacity=4096)
+    lat.step(900)
+    d = lat.cycle_change([600, 400])
+    assert d[0] == -1.0 and d[1] >= 0.0                 # instance 0 lacks two beats of history
+    lat.step(1000)
+    d = lat.cycle_change([600, 400])
+    for q, T in enumerate((600, 400)):
+        w = lat.waves(q)
+        cur, prev = w[-T:], w[-2 * T:-T]
+        ref = max(np.abs(cur[:, c] - prev[:, c]).max() / np.abs(prev[:, c]).max()
+                  for c in (1, 2, 5, 6))
+        assert d[q] == pytest.approx(ref, rel=1e-12)
+
+
+def test_autotune_keeps_trajectory(Lattice):
+    inst = configs.lv_tube(period=600)
+    a = Lattice([inst], precision="f64")
+    a.step(10)
+    block, minb = a.autotune(iters=3)
+    assert block in (64, 128, 192, 256) and minb in (5, 6, 8)
+    a.step(190)
+    b = Lattice([inst], precision="f64")
+    b.step(200)
+    assert np.abs(a.populations(0) - b.populations(0)).max() < 1e-15
+    assert np.array_equal(a.waves(0), b.waves(0))
+
+
+def test_set_0d_state_round_trip(Lattice):
+    inst = configs.lv_tube(period=600)
+    lat = Lattice([inst], precision="f32")
+    lat.set_0d_state(0, 1, 0.0042)
+    lat.set_0d_state(0, 0, 0.0031, valve_open=1.0, Td=-5.0)
+    s1, s0 = lat.state_0d(0, 1), lat.state_0d(0, 0)
+    assert s1[4] == 0.0042 and s0[4] == 0.0031 and s0[6] == 1.0 and s0[7] == -5.0
+
+
+def test_run_to_periodic_small_batch(Lattice):
+    from paper_2112_05258_gb300.periodic import run_to_periodic
+    insts = [configs.lv_tube(period=T) for T in (400, 600)]
+    lat = Lattice(insts, precision="f32", wave_capacity=4096)
+    cycles, steps = run_to_periodic(lat, [400, 600], tol=0.01, max_cycles=30)
+    assert (cycles > 1).all()
+    d = lat.cycle_change([400, 600])
+    assert (d <= 0.02).all()
+
+
+def test_uneven_batch_equals_single(Lattice):
+    insts, params = batch.tube_batch(6, seed=5)
+    lat = Lattice(insts, precision="f32")
+    lat.step(300)
+    for q in (0, 3, 5):
+        single = Lattice([insts[q]], precision="f32")
+        single.step(300)
+        assert np.array_equal(lat.populations(q), single.populations(0))
+        assert np.array_equal(lat.waves(q), single.waves(0))
