@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "liblbm.so")
-SOURCES = ["lbm_api.cu", "lbm_kernels.cu", "lbm_ib.cu", "lbm_layout.cu", "lbm_noalloc.cu"]
+SOURCES = ["lbm_api.cu", "lbm_kernels.cu", "lbm_ib.cu", "lbm_layout.cu", "lbm_noalloc.cu", "lbm_mlp.cu"]
 HEADERS = ["lbm_internal.h", "lbm_kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
@@ -40,7 +40,7 @@ def build(force: bool = False, verbose: bool = False, extra=None, out_dir: str =
     os.makedirs(out_dir, exist_ok=True)
     so = os.path.join(out_dir, "liblbm.so")
     inc = os.path.join(os.path.dirname(HERE), "include")
-    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(inc, "lbm.h"), __file__]
+    hdrs = [os.path.join(CSRC, h) for h in HEADERS] + [os.path.join(inc, f) for f in os.listdir(inc)] + [__file__]
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

@@ -341,11 +341,9 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
              ck(dalloc_bytes(h, &h->vband, 4 * n * h->rbytes), "vband");
     }
     {
-        std::vector<int> ib2;
-        for (auto &ip : L.inst) {
-            ib2.push_back(ip.bc_first);
-            ib2.push_back(ip.n_bc);
-        }
+        std::vector<int> ib2;  // bc_first of every instance, then n_bc of every instance
+        for (auto &ip : L.inst) ib2.push_back(ip.bc_first);
+        for (auto &ip : L.inst) ib2.push_back(ip.n_bc);
         for (size_t q = 0; q < L.inst.size(); q++)
             h->max_inst_cells = std::max<int64_t>(h->max_inst_cells, L.inst_cell_end[q] - L.inst_cell_begin[q]);
         if (ok) ok = ck(upload(h, &h->inst_bc, ib2), "instances") &&
@@ -680,8 +678,8 @@ lbm_status lbm_cycle_change(lbm_handle *h, const int64_t *period, double *delta)
     }
     CK(h, cudaSetDevice(h->device));
     CK(h, cudaMemcpyAsync(h->inst_period, per.data(), ni * sizeof(long long), cudaMemcpyHostToDevice, h->stream));
-    CK(h, launch_cycle_change(h->bp, h->inst_bc, h->inst_bc + 1, h->inst_period, (long long)h->steps, h->inst_delta, ni,
-                              h->stream));
+    CK(h, launch_cycle_change(h->bp, h->inst_bc, h->inst_bc + ni, h->inst_period, (long long)h->steps, h->inst_delta,
+                              ni, h->stream));
     CK(h, cudaMemcpyAsync(delta, h->inst_delta, ni * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     return LBM_OK;

@@ -20,9 +20,13 @@ def lib():
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", src)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            src = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, f)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_every_declared_symbol_is_exported(lib):
@@ -30,8 +34,8 @@ def test_every_declared_symbol_is_exported(lib):
     assert len(names) >= 15
     for n in names:
         assert hasattr(lib, n), n
-    from paper_2112_05258_gb300 import lbm
-    assert sorted(lbm.EXPORTS) == names
+    from paper_2112_05258_gb300 import lbm, mlp
+    assert sorted(lbm.EXPORTS + mlp.EXPORTS) == names
 
 
 def _cfg(lbm, node, tau=0.8, bcs=(), precision=0, graph_steps=0):

@@ -27,12 +27,12 @@ PARAM_NAMES = ("R_p", "C", "R_d", "E_max", "E_min", "period")
 
 
 def draw_params(rng: np.random.Generator, n: int, e_min_range=(0.06, 0.06),
-                period_step: int = 1) -> np.ndarray:
+                period_step: int = 1, period_range=(2000, 6000)) -> np.ndarray:
     """(n, 6) array of (R_p, C, R_d, E_max, E_min, period)."""
     lo, hi = math.log(0.5), math.log(1.5)
     Rp = 0.05 * np.exp(rng.uniform(lo, hi, n))
     Rd = 1.0 * np.exp(rng.uniform(lo, hi, n))
-    T = rng.uniform(2000, 6000, n)
+    T = rng.uniform(period_range[0], period_range[1], n)
     T = np.round(T / period_step) * period_step
     C = 1.5 * T / 1.0 * np.exp(rng.uniform(lo, hi, n))
     Emax = rng.uniform(1.5, 3.0, n)
@@ -40,14 +40,16 @@ def draw_params(rng: np.random.Generator, n: int, e_min_range=(0.06, 0.06),
     return np.stack([Rp, C, Rd, Emax, Emin, T], axis=1)
 
 
-def lv_tube_instance(params, radius: float, length: int, tau: float = 0.8) -> Instance:
+def lv_tube_instance(params, radius: float, length: int, tau: float = 0.8,
+                     kappa: float = configs.LV_KAPPA) -> Instance:
     """Rigid tube of the given radius and length with an LV inlet and an RCR
-    outlet set from one row of :func:`draw_params`."""
+    outlet set from one row of :func:`draw_params` (``kappa``: the lattice
+    elastance scale)."""
     Rp, C, Rd, Emax, Emin, T = (float(v) for v in params)
     n_xy = int(math.ceil(2 * radius + 4))
     node = geometry.straight_tube(n_xy, n_xy, int(length), radius)
     inst = Instance(node=node, tau=tau, name=f"lv_tube_R{radius:.2f}_L{length}_T{int(T)}")
-    inst.boundaries.append(configs.lv_boundary(period=int(T), e_max=Emax, e_min=Emin))
+    inst.boundaries.append(configs.lv_boundary(period=int(T), e_max=Emax, e_min=Emin, kappa=kappa))
     inst.boundaries.append(Boundary(BC_RCR, 2, -1, [Rp, C, Rd, 0.0]))
     return inst
 
@@ -61,11 +63,13 @@ def tube_batch(n: int = 256, seed: int = 0):
     return [lv_tube_instance(params[q], R[q], int(L[q])) for q in range(n)], params
 
 
-def lv_sweep(n: int, seed: int, radius: float = 6.0, length: int = 128, period_step: int = 100):
+def lv_sweep(n: int, seed: int, radius: float = 6.0, length: int = 128, period_step: int = 100,
+             period_range=(2000, 6000), kappa: float = configs.LV_KAPPA):
     """Returns (instances, params) for the warm-start study: one tube
     geometry, six 0D parameters drawn per instance (periods on a grid of
     ``period_step`` steps so that a batch can be read at every instance's
     cycle phase 0 after a whole number of chunks)."""
     rng = np.random.default_rng(seed)
-    params = draw_params(rng, n, e_min_range=(0.05, 0.07), period_step=period_step)
-    return [lv_tube_instance(params[q], radius, length) for q in range(n)], params
+    params = draw_params(rng, n, e_min_range=(0.05, 0.07), period_step=period_step,
+                         period_range=period_range)
+    return [lv_tube_instance(params[q], radius, length, kappa=kappa) for q in range(n)], params
