@@ -138,6 +138,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(x: float, world: int, device="cuda") -> float:
+    """The maximum of x over all ranks (replicas: the slowest rank decides)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(cells: int, steps: int, world: int, ms: float) -> float:
+    """Whole-job MLUPS of `world` replicas that each update `cells` cells for
+    `steps` steps in `ms` milliseconds (the maximum over ranks)."""
+    return cells * steps * world / (ms * 1e-3) / 1e6
+
+
 def cpu_baseline(inst, seconds: float):
     """Times the FP64 oracle on one instance for about ``seconds``."""
     import oracle
@@ -206,7 +223,7 @@ def main():
     info = lat.info()
     tuned = None
     if args.autotune:
-        tuned = dict(zip(("block", "min_blocks_per_sm"), lat.autotune(iters=10)))
+        tuned = dict(zip(("block", "min_blocks_per_sm", "cells_per_thread"), lat.autotune(iters=10)))
     cells = info.fluid_cells
     kernels_per_step = 3 + (2 if info.ib_nodes else 0)
 
@@ -215,12 +232,6 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{local}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
 
     # warm-up (also captures the CUDA graphs)
     lat.step(max(3, args.warmup))
@@ -236,8 +247,8 @@ def main():
     lat.sync()
     barrier()
     clk = clocks.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1))
-    value = cells * args.steps * world / (ms * 1e-3) / 1e6
+    ms = max_over_ranks(e0.elapsed_time(e1), world, device=f"cuda:{local}")
+    value = replica_throughput(cells, args.steps, world, ms)
 
     # dominant kernel: stream-collide, each launch bracketed by events on the same stream
     k_steps = min(args.steps, 400)
@@ -265,8 +276,8 @@ def main():
             lat.state_0d(0, k)
     lat.sync()
     barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e = {"value": cells * e2e_steps * world / e2e_s / 1e6, "unit": "MLUPS",
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, device=f"cuda:{local}")
+    e2e = {"value": replica_throughput(cells, e2e_steps, world, e2e_s * 1e3), "unit": "MLUPS",
            "h2d_bytes_per_step": int(rcr.nbytes), "d2h_bytes_per_step": int(8 * 8 * nbc),
            "steps": e2e_steps}
 

@@ -106,6 +106,7 @@ typedef struct {
     int graph_steps;   /* steps per captured CUDA graph (even, >= 2); 0 = 64 */
     int wave_capacity; /* waveform ring-buffer length in steps; 0 = 8192 */
     int block_size;    /* threads per block of the stream-collide kernel, multiple of 32 in [32, 256]; 0 = 128 */
+    int ib_threads_per_node; /* threads of the immersed-boundary node kernel per wall node: 1, 2 or 4; 0 = 1 */
 } lbm_config;
 
 typedef struct lbm_handle lbm_handle;
@@ -188,11 +189,14 @@ lbm_status lbm_set_0d_state(lbm_handle *h, int inst, int bc, const double *state
 lbm_status lbm_cycle_change(lbm_handle *h, const int64_t *period, double *delta);
 
 /* Autotuner: times the stream-collide kernel for block sizes 64, 128, 192,
- * 256 and three register/occupancy variants (at least 5, 6 or 8 resident
- * 256-thread blocks per SM), `iters` launches each, on the handle's current
- * state (which is left unchanged), and keeps the fastest.  Returns the chosen
- * block size and minimum-blocks variant. */
-lbm_status lbm_autotune(lbm_handle *h, int iters, int *block, int *min_blocks);
+ * 256 and five register/occupancy variants ({min resident 256-thread blocks
+ * per SM, cells per thread} = {6,1}, {8,1}, {5,1}, {4,2}, {3,2}), `iters`
+ * launches each, on the handle's current state (which is left unchanged),
+ * and keeps the fastest.  Returns the chosen block size, minimum blocks and
+ * cells per thread; times_ms (NULL or 20 doubles, variant-major) receives the
+ * mean launch time of every candidate. */
+lbm_status lbm_autotune(lbm_handle *h, int iters, int *block, int *min_blocks, int *cells_per_thread,
+                        double *times_ms);
 
 /* Kernel timing for roofline measurement.  While enabled, lbm_step launches
  * its kernels directly (no graph) and brackets every stream-collide launch

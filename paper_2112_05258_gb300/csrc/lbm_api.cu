@@ -120,6 +120,9 @@ lbm_status check_config(const lbm_config *cfg, std::string &why) {
     if (cfg->precision < 0 || cfg->precision > 3) return why = "precision out of range", LBM_ERR_ARG;
     if (cfg->n_instances <= 0 || !cfg->inst) return why = "no instances", LBM_ERR_ARG;
     if (cfg->graph_steps < 0 || (cfg->graph_steps % 2) != 0) return why = "graph_steps must be even", LBM_ERR_ARG;
+    if (cfg->ib_threads_per_node != 0 && cfg->ib_threads_per_node != 1 && cfg->ib_threads_per_node != 2 &&
+        cfg->ib_threads_per_node != 4)
+        return why = "ib_threads_per_node must be 0, 1, 2 or 4", LBM_ERR_ARG;
     if (cfg->block_size != 0 && (cfg->block_size < 32 || cfg->block_size > 256 || cfg->block_size % 32))
         return why = "block_size must be a multiple of 32 in [32, 256]", LBM_ERR_ARG;
     for (int q = 0; q < cfg->n_instances; q++) {
@@ -400,6 +403,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
     h->ibp.ks = h->ibks;
     h->ibp.pinned = h->ibpin;
     h->ibp.vband = h->vband;
+    h->ibp.threads_per_node = cfg->ib_threads_per_node ? cfg->ib_threads_per_node : 1;
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(LBM_ERR_CUDA, "set-up failed");
     *out = h;
     return LBM_OK;
@@ -685,8 +689,9 @@ lbm_status lbm_cycle_change(lbm_handle *h, const int64_t *period, double *delta)
     return LBM_OK;
 }
 
-lbm_status lbm_autotune(lbm_handle *h, int iters, int *block, int *min_blocks) {
-    if (!h || iters < 1 || !block || !min_blocks) return fail(h, LBM_ERR_ARG, "bad arguments");
+lbm_status lbm_autotune(lbm_handle *h, int iters, int *block, int *min_blocks, int *cells_per_thread,
+                        double *times_ms) {
+    if (!h || iters < 1 || !block || !min_blocks || !cells_per_thread) return fail(h, LBM_ERR_ARG, "bad arguments");
     CK(h, cudaSetDevice(h->device));
     CK(h, cudaStreamSynchronize(h->stream));
     KParams kp = h->kp;
@@ -708,6 +713,7 @@ lbm_status lbm_autotune(lbm_handle *h, int iters, int *block, int *min_blocks) {
             CK(h, cudaEventSynchronize(e1));
             float ms = 0.f;
             CK(h, cudaEventElapsedTime(&ms, e0, e1));
+            if (times_ms) times_ms[4 * v + bi] = ms / iters;
             if (ms < best) {
                 best = ms;
                 bb = blocks[bi];
@@ -723,6 +729,7 @@ lbm_status lbm_autotune(lbm_handle *h, int iters, int *block, int *min_blocks) {
     h->variant = bv;
     *block = bb;
     *min_blocks = stream_collide_min_blocks(bv);
+    *cells_per_thread = stream_collide_cells_per_thread(bv);
     return LBM_OK;
 }
 

@@ -5,11 +5,11 @@
 //   k_band_moments  unforced velocity j/rho0 of f(t_n) at every band cell
 //                   (the cells within reach of a wall node's kernel support)
 //                   and b = 0 there; both as one 4-vector per cell
-//   k_ib_nodes      one thread per wall node: gather V_f over the 64 support
-//                   cells of the 4-point cosine delta, penalty integral and
-//                   force F = alpha I + beta (V_f - V_s) on the fluid,
-//                   spreading of F delta dA with one vector atomic per cell,
-//                   spring update.
+//   k_ib_nodes      1, 2 or 4 threads per wall node: gather V_f over the 64
+//                   support cells of the 4-point cosine delta, penalty
+//                   integral and force F = alpha I + beta (V_f - V_s) on the
+//                   fluid, spreading of F delta dA with one vector atomic per
+//                   cell, spring update.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -36,8 +36,8 @@ __global__ void k_band_moments(const S *__restrict__ fin, KParams p, IbKParams i
     const int c = ib.band[t];
     const uint32_t fl = p.flags[c];
     const size_t N = (size_t)p.n;
-    int r = p.chunk_row[c >> 5];
-    while (p.rows[r + 1].off <= c) r++;
+    const int2 ch = reinterpret_cast<const int2 *>(p.chunk_row)[c >> 5];
+    const int r = ch.x + __popc((uint32_t)ch.y & ((2u << (c & 31)) - 1u));
     const int x = p.rows[r].x0 + (c - p.rows[r].off);
     R jx = 0, jy = 0, jz = 0;
 #pragma unroll
@@ -78,16 +78,22 @@ __device__ __forceinline__ void vec_atomic_add(double4a *a, double4a v) {
     atomicAdd(&a->z, v.z);
 }
 
-// One thread per wall node; a warp holds 32 consecutive nodes of a ring, so
-// at each support offset its atomics land on (mostly) different cells.  The
-// support is walked as 16 lattice lines (dy, dz) of 4 cells along x, with
-// one row lookup per line.
-template <class S>
+// TPN threads per wall node (1, 2 or 4); lane q of a node's group owns the
+// support planes dz = q * PL .. q * PL + PL - 1 (PL = 4 / TPN) of the 4-point
+// cosine delta, walks their lattice lines (dy) with one row lookup per line,
+// and keeps the line bases and a mask of its valid support cells in
+// registers for the spreading pass.  A warp holds 32 / TPN consecutive nodes
+// of a ring.  The group's partial velocities are summed with butterfly
+// shuffles, which every lane evaluates in the same order, so all lanes
+// compute the same penalty force; lane 0 writes the node state.
+template <class S, int TPN>
 __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib) {
     using R = typename IbStorage<S>::R;
     using V = typename Vec4<R>::T;
-    const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= ib.n_nodes) return;
+    constexpr int PL = 4 / TPN;
+    const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = gt / TPN, q = gt % TPN;
+    if (s >= ib.n_nodes) return;  // the lanes of a node leave together
     const InstParam &ip = ib.inst[ib.node_inst[s]];
     const int ny = ip.ny, nz = ip.nz;
     double X[3];
@@ -107,17 +113,23 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib) {
     const V *vb = static_cast<const V *>(ib.vband);
     R vx = 0, vy = 0, vz = 0;
     bool out_of_band = false;
+    int lb[4 * PL];
+    uint64_t valid = 0;  // bit dx + 4 (dy + 4 j) for the lane's plane j
 #pragma unroll
-    for (int dz = 0; dz < 4; dz++) {
+    for (int j = 0; j < PL; j++) {
+        const int dz = q * PL + j;
         const int z = i0[2] + dz - 1;
+        const R wz = w[2][0] * (dz == 0) + w[2][1] * (dz == 1) + w[2][2] * (dz == 2) + w[2][3] * (dz == 3);
 #pragma unroll
         for (int dy = 0; dy < 4; dy++) {
             const int y = i0[1] + dy - 1;
+            lb[dy + 4 * j] = 0;
             if (y < 0 || y >= ny || z < 0 || z >= nz) continue;
             const int r = ib.rowid[ip.rowid_off + y + ny * z];
             if (r < 0) continue;
             const int x0 = p.rows[r].x0, len = p.rows[r].len, base = p.rows[r].off - x0;
-            const R wyz = w[1][dy] * w[2][dz];
+            lb[dy + 4 * j] = base;
+            const R wyz = w[1][dy] * wz;
 #pragma unroll
             for (int dx = 0; dx < 4; dx++) {
                 const int x = i0[0] + dx - 1;
@@ -129,6 +141,7 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib) {
                     out_of_band = true;
                     continue;
                 }
+                valid |= 1ull << (dx + 4 * (dy + 4 * j));
                 const V v = vb[c];
                 const R d = w[0][dx] * wyz;
                 vx += v.x * d;
@@ -138,6 +151,15 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib) {
         }
     }
     if (out_of_band) atomicOr(p.status, 2u);
+    if (TPN > 1) {
+        const unsigned grp = ((1u << TPN) - 1u) << ((threadIdx.x & 31) & ~(TPN - 1));
+#pragma unroll
+        for (int o = 1; o < TPN; o <<= 1) {
+            vx += __shfl_xor_sync(grp, vx, o, TPN);
+            vy += __shfl_xor_sync(grp, vy, o, TPN);
+            vz += __shfl_xor_sync(grp, vz, o, TPN);
+        }
+    }
     const double Vf[3] = {(double)vx, (double)vy, (double)vz};
     double F[3], Vs[3];
 #pragma unroll
@@ -146,41 +168,31 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib) {
         const double dv = Vf[a] - Vs[a];
         const double I = ib.I[3 * s + a] + dv;
         F[a] = ip.alpha * I + ip.beta * dv;
-        ib.I[3 * s + a] = I;
-        ib.F[3 * s + a] = F[a];
-        ib.Vf[3 * s + a] = Vf[a];
+        if (q == 0) {
+            ib.I[3 * s + a] = I;
+            ib.F[3 * s + a] = F[a];
+            ib.Vf[3 * s + a] = Vf[a];
+        }
     }
     const R dA = (R)ib.dA[s];
     const R Fx = (R)F[0] * dA, Fy = (R)F[1] * dA, Fz = (R)F[2] * dA;
     V *b = static_cast<V *>(const_cast<void *>(p.b));
 #pragma unroll
-    for (int dz = 0; dz < 4; dz++) {
-        const int z = i0[2] + dz - 1;
-#pragma unroll
-        for (int dy = 0; dy < 4; dy++) {
-            const int y = i0[1] + dy - 1;
-            if (y < 0 || y >= ny || z < 0 || z >= nz) continue;
-            const int r = ib.rowid[ip.rowid_off + y + ny * z];
-            if (r < 0) continue;
-            const int x0 = p.rows[r].x0, len = p.rows[r].len, base = p.rows[r].off - x0;
-            const R wyz = w[1][dy] * w[2][dz];
-#pragma unroll
-            for (int dx = 0; dx < 4; dx++) {
-                const int x = i0[0] + dx - 1;
-                if (x < x0 || x >= x0 + len) continue;
-                const int c = base + x;
-                if ((p.flags[c] & (FL_ACTIVE | FL_BAND)) != (FL_ACTIVE | FL_BAND)) continue;
-                const R d = w[0][dx] * wyz;
-                V add;
-                add.x = Fx * d;
-                add.y = Fy * d;
-                add.z = Fz * d;
-                add.w = 0;
-                vec_atomic_add(&b[c], add);
-            }
-        }
+    for (int k = 0; k < 16 * PL; k++) {
+        if (!((valid >> k) & 1ull)) continue;
+        const int dx = k & 3, dy = (k >> 2) & 3, j = k >> 4;
+        const int dz = q * PL + j;
+        const R wz = w[2][0] * (dz == 0) + w[2][1] * (dz == 1) + w[2][2] * (dz == 2) + w[2][3] * (dz == 3);
+        const int c = lb[dy + 4 * j] + i0[0] + dx - 1;
+        const R d = w[0][dx] * (w[1][dy] * wz);
+        V add;
+        add.x = Fx * d;
+        add.y = Fy * d;
+        add.z = Fz * d;
+        add.w = 0;
+        vec_atomic_add(&b[c], add);
     }
-    if (!ib.pinned[s]) {
+    if (q == 0 && !ib.pinned[s]) {
 #pragma unroll
         for (int a = 0; a < 3; a++) {
             const double acc = (-ib.ks[s] * (X[a] - ib.X0[3 * s + a]) - F[a]) / ip.ms;
@@ -191,27 +203,34 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib) {
     }
 }
 
+template <class S> static void launch_nodes(const KParams &p, const IbKParams &ib, cudaStream_t st) {
+    const int tpn = ib.threads_per_node;
+    const int grid = (int)(((long long)ib.n_nodes * tpn + 127) / 128);
+    if (tpn == 1) k_ib_nodes<S, 1><<<grid, 128, 0, st>>>(p, ib);
+    else if (tpn == 2) k_ib_nodes<S, 2><<<grid, 128, 0, st>>>(p, ib);
+    else k_ib_nodes<S, 4><<<grid, 128, 0, st>>>(p, ib);
+}
+
 cudaError_t launch_ib(int prec, const void *fin, const KParams &p, const IbKParams &ib, cudaStream_t st) {
     if (ib.n_nodes == 0) return cudaSuccess;
     const int block = 256;
     const int gb = (ib.n_band + block - 1) / block;
-    const int gn = (ib.n_nodes + 127) / 128;
     switch (prec) {
     case 0:
         if (gb) k_band_moments<float><<<gb, block, 0, st>>>(static_cast<const float *>(fin), p, ib);
-        k_ib_nodes<float><<<gn, 128, 0, st>>>(p, ib);
+        launch_nodes<float>(p, ib, st);
         break;
     case 1:
         if (gb) k_band_moments<__half><<<gb, block, 0, st>>>(static_cast<const __half *>(fin), p, ib);
-        k_ib_nodes<__half><<<gn, 128, 0, st>>>(p, ib);
+        launch_nodes<__half>(p, ib, st);
         break;
     case 2:
         if (gb) k_band_moments<__nv_bfloat16><<<gb, block, 0, st>>>(static_cast<const __nv_bfloat16 *>(fin), p, ib);
-        k_ib_nodes<__nv_bfloat16><<<gn, 128, 0, st>>>(p, ib);
+        launch_nodes<__nv_bfloat16>(p, ib, st);
         break;
     default:
         if (gb) k_band_moments<double><<<gb, block, 0, st>>>(static_cast<const double *>(fin), p, ib);
-        k_ib_nodes<double><<<gn, 128, 0, st>>>(p, ib);
+        launch_nodes<double>(p, ib, st);
         break;
     }
     return cudaGetLastError();

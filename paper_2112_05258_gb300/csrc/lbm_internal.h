@@ -96,7 +96,8 @@ struct BcState {
 struct Layout {
     int64_t n_stored = 0, n_fluid = 0, n_box = 0;
     std::vector<RowInfo> rows;          // + one sentinel row with off = n_stored
-    std::vector<int32_t> chunk_row;     // row of the first cell of each CHUNK
+    std::vector<int32_t> chunk_row;     // per CHUNK of 32 cells: {row of its first cell, mask of the
+                                        // lanes 1..31 whose cell begins a new row}, interleaved
     std::vector<uint32_t> flags;        // per stored cell
     std::vector<int64_t> cell_box;      // per stored cell: box index within its instance
     std::vector<int32_t> cell_inst;     // per stored cell

@@ -18,7 +18,7 @@ struct KParams {
     long long n;                // stored cells = population stride
     const uint32_t *flags;      // per cell
     const RowInfo *rows;        // rows + sentinel
-    const int32_t *chunk_row;   // per 32-cell chunk
+    const int32_t *chunk_row;   // per 32-cell chunk: {row of its first cell, new-row lane mask}
     const double *omega;        // per instance, 1/tau
     const void *b;              // force density b, 4 x compute type per cell (x, y, z, unused)
     void *aux;                  // first-layer macros (sum s, jx, jy, jz), compute type, 4 x n
@@ -62,12 +62,14 @@ struct IbKParams {
     const double *X0, *dA, *ks;
     const uint8_t *pinned;
     void *vband;                // unforced velocity at band cells, 4 x compute type per cell
+    int threads_per_node;       // 1, 2 or 4 threads of the node kernel per wall node
 };
 
-// variant: 0 = at least 6 blocks of 256 per SM (40 registers), 1 = 8 blocks
-// (32 registers), 2 = 5 blocks (48 registers)
-constexpr int SC_VARIANTS = 3;
+// variants {min resident 256-thread blocks per SM, cells per thread}:
+// 0 {6, 1} (40 registers), 1 {8, 1} (32), 2 {5, 1} (48), 3 {4, 2}, 4 {3, 2}
+constexpr int SC_VARIANTS = 5;
 int stream_collide_min_blocks(int variant);
+int stream_collide_cells_per_thread(int variant);
 cudaError_t launch_stream_collide(int prec, const void *fin, void *fout, const KParams &p, int block,
                                   int variant, cudaStream_t s);
 cudaError_t launch_boundary(int prec, void *f, const KParams &p, const BcKParams &q, cudaStream_t s);

@@ -97,15 +97,19 @@ std::string build_layout(const lbm_config *cfg, Layout &L) {
     sent.off = (int32_t)cell;
     sent.inst = -1;
     L.rows.push_back(sent);
-    // chunk -> row
+    // chunk -> {row of the first cell, lanes starting a new row}
     const int64_t nchunk = (cell + CHUNK - 1) / CHUNK;
-    L.chunk_row.assign(nchunk, 0);
+    L.chunk_row.assign(2 * nchunk, 0);
     {
         size_t r = 0;
         for (int64_t c = 0; c < nchunk; c++) {
-            int64_t first = c * CHUNK;
+            const int64_t first = c * CHUNK;
             while (L.rows[r + 1].off <= first) r++;
-            L.chunk_row[c] = (int32_t)r;
+            L.chunk_row[2 * c] = (int32_t)r;
+            uint32_t mask = 0;
+            for (size_t rr = r + 1; rr + 1 < L.rows.size() && L.rows[rr].off < first + CHUNK; rr++)
+                mask |= 1u << (L.rows[rr].off - first);
+            L.chunk_row[2 * c + 1] = (int32_t)mask;
         }
     }
     // per-cell flags, box index, instance

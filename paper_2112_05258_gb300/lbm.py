@@ -46,7 +46,8 @@ class Config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("n_instances", ctypes.c_int),
                 ("inst", ctypes.POINTER(InstanceDesc)), ("stream", ctypes.c_void_p),
                 ("device", ctypes.c_int), ("graph_steps", ctypes.c_int),
-                ("wave_capacity", ctypes.c_int), ("block_size", ctypes.c_int)]
+                ("wave_capacity", ctypes.c_int), ("block_size", ctypes.c_int),
+                ("ib_threads_per_node", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -98,7 +99,8 @@ def load(path: Optional[str] = None):
     L.lbm_init_equilibrium.argtypes = [H, ctypes.c_int, _dp, _dp, _dp, _dp]
     L.lbm_set_0d_state.argtypes = [H, ctypes.c_int, ctypes.c_int, _dp]
     L.lbm_cycle_change.argtypes = [H, ctypes.POINTER(ctypes.c_int64), _dp]
-    L.lbm_autotune.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]
+    L.lbm_autotune.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                               ctypes.POINTER(ctypes.c_int), _dp]
     L.lbm_boundary_flux_noalloc.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
     for name in EXPORTS:
@@ -127,7 +129,7 @@ class Lattice:
 
     def __init__(self, instances: Sequence, precision="f32", device: int = 0,
                  stream: Optional[int] = None, graph_steps: int = 0, wave_capacity: int = 0,
-                 block_size: int = 0):
+                 block_size: int = 0, ib_threads_per_node: int = 0):
         L = load()
         if isinstance(precision, str):
             precision = PRECISIONS[precision.lower()]
@@ -176,7 +178,8 @@ class Lattice:
         cfg = Config(precision=int(precision), n_instances=n,
                      inst=ctypes.cast(descs, ctypes.POINTER(InstanceDesc)),
                      stream=ctypes.c_void_p(stream or 0), device=device, graph_steps=graph_steps,
-                     wave_capacity=wave_capacity, block_size=block_size)
+                     wave_capacity=wave_capacity, block_size=block_size,
+                     ib_threads_per_node=ib_threads_per_node)
         h = ctypes.c_void_p()
         st = L.lbm_create(ctypes.byref(cfg), ctypes.byref(h))
         self._keep = None
@@ -285,10 +288,16 @@ class Lattice:
         self._ck(load().lbm_cycle_change(self._h, per.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _p(out)))
         return out
 
-    def autotune(self, iters: int = 20):
-        b, m = ctypes.c_int(), ctypes.c_int()
-        self._ck(load().lbm_autotune(self._h, int(iters), ctypes.byref(b), ctypes.byref(m)))
-        return b.value, m.value
+    def autotune(self, iters: int = 20, return_times: bool = False):
+        """Picks the fastest stream-collide launch shape; returns (block,
+        min_blocks_per_sm, cells_per_thread) and, optionally, the (5, 4) table
+        of mean launch times in ms (variants x block sizes 64, 128, 192, 256)."""
+        b, m, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        times = np.zeros(20)
+        self._ck(load().lbm_autotune(self._h, int(iters), ctypes.byref(b), ctypes.byref(m), ctypes.byref(c),
+                                     _p(times)))
+        out = (b.value, m.value, c.value)
+        return (out, times.reshape(5, 4)) if return_times else out
 
     def info(self) -> Info:
         i = Info()

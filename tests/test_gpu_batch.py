@@ -64,8 +64,9 @@ def test_autotune_keeps_trajectory(Lattice):
     inst = configs.lv_tube(period=600)
     a = Lattice([inst], precision="f64")
     a.step(10)
-    block, minb = a.autotune(iters=3)
-    assert block in (64, 128, 192, 256) and minb in (5, 6, 8)
+    (block, minb, cpt), times = a.autotune(iters=3, return_times=True)
+    assert block in (64, 128, 192, 256) and minb in (3, 4, 5, 6, 8) and cpt in (1, 2)
+    assert times.shape == (5, 4) and (times > 0).all()
     a.step(190)
     b = Lattice([inst], precision="f64")
     b.step(200)

@@ -165,6 +165,21 @@ def test_graph_equals_direct_launches(Lattice):
     assert np.array_equal(g.waves(0), d.waves(0))
 
 
+def test_graph_equals_direct_launches_with_ib(Lattice):
+    # graphs run the non-band cells on a second stream beside the IB chain;
+    # direct launches run one sequence: the same per-cell arithmetic, only the
+    # order of the spreading atomics may differ
+    inst = configs.ib_tube()
+    for prec, tol in (("f64", 1e-14), ("f32", 1e-6)):
+        g = Lattice([inst], precision=prec, graph_steps=8)
+        g.step(203)
+        d = Lattice([inst], precision=prec)
+        d.set_kernel_timing(True)
+        d.step(203)
+        assert np.abs(g.populations(0) - d.populations(0)).max() < tol
+        assert np.abs(g.waves(0)[:, 1:] - d.waves(0)[:, 1:]).max() < tol
+
+
 def test_unstable_state_is_reported(Lattice):
     from paper_2112_05258_gb300 import LBMError
     inst = Instance(node=geometry.closed_box(10, 10, 10), tau=0.52)
