@@ -52,6 +52,8 @@ struct lbm_handle {
     double *ibX = nullptr, *ibVs = nullptr, *ibI = nullptr, *ibF = nullptr, *ibVf = nullptr;
     double *ibX0 = nullptr, *ibdA = nullptr, *ibks = nullptr;
     uint8_t *ibpin = nullptr;
+    int32_t *iblines = nullptr, *ibref = nullptr;
+    uint64_t *ibmask = nullptr;
     double *rd_f19 = nullptr, *rd_mac = nullptr;  // read-out scratch, largest instance (allocated on first use)
     int64_t max_inst_cells = 0;
     int variant = 0;  // stream-collide occupancy variant (see launch_stream_collide)
@@ -340,7 +342,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
              ck(upload(h, &h->ibVs, zero), "ib") && ck(upload(h, &h->ibI, zero), "ib") &&
              ck(upload(h, &h->ibF, zero), "ib") && ck(upload(h, &h->ibVf, zero), "ib") &&
              ck(upload(h, &h->ibdA, L.ib_dA), "ib") && ck(upload(h, &h->ibks, L.ib_ks), "ib") &&
-             ck(upload(h, &h->ibpin, L.ib_pinned), "ib") &&
+             ck(upload(h, &h->ibpin, L.ib_pinned), "ib") && ck(upload(h, &h->iblines, L.ib_lines), "ib") &&
+             ck(upload(h, &h->ibmask, L.ib_mask), "ib") && ck(upload(h, &h->ibref, L.ib_ref), "ib") &&
              ck(dalloc_bytes(h, &h->vband, 4 * n * h->rbytes), "vband");
     }
     {
@@ -404,6 +407,9 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
     h->ibp.pinned = h->ibpin;
     h->ibp.vband = h->vband;
     h->ibp.threads_per_node = cfg->ib_threads_per_node ? cfg->ib_threads_per_node : 1;
+    h->ibp.lines = h->iblines;
+    h->ibp.mask = h->ibmask;
+    h->ibp.ref = h->ibref;
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(LBM_ERR_CUDA, "set-up failed");
     *out = h;
     return LBM_OK;

@@ -80,9 +80,10 @@ __device__ __forceinline__ void vec_atomic_add(double4a *a, double4a v) {
 
 // TPN threads per wall node (1, 2 or 4); lane q of a node's group owns the
 // support planes dz = q * PL .. q * PL + PL - 1 (PL = 4 / TPN) of the 4-point
-// cosine delta, walks their lattice lines (dy) with one row lookup per line,
-// and keeps the line bases and a mask of its valid support cells in
-// registers for the spreading pass.  A warp holds 32 / TPN consecutive nodes
+// cosine delta.  The lattice lines and fluid cells of the support come from
+// the node's precomputed table (no row lookup, no flag loads), and the line
+// bases and a mask of the valid support cells stay in registers for the
+// spreading pass.  A warp holds 32 / TPN consecutive nodes
 // of a ring.  The group's partial velocities are summed with butterfly
 // shuffles, which every lane evaluates in the same order, so all lanes
 // compute the same penalty force; lane 0 writes the node state.
@@ -110,43 +111,47 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib) {
 #pragma unroll
         for (int k = 0; k < 4; k++) w[a][k] = delta_weight<R>(Sn, Cs, k);
     }
+    // support cells through the node's precomputed line table and fluid mask
+    // (box of 6^3 cells around its reference cell; the node may move by less
+    // than one cell from it, else the status word reports it)
+    int d[3];
+    bool out_of_band = false;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        d[a] = i0[a] - ib.ref[3 * s + a];
+        out_of_band |= (d[a] < -1 || d[a] > 1);
+    }
     const V *vb = static_cast<const V *>(ib.vband);
     R vx = 0, vy = 0, vz = 0;
-    bool out_of_band = false;
     int lb[4 * PL];
     uint64_t valid = 0;  // bit dx + 4 (dy + 4 j) for the lane's plane j
+    if (!out_of_band) {
+        const int32_t *lines = ib.lines + 36 * (size_t)s;
+        const uint64_t m0 = ib.mask[4 * (size_t)s], m1 = ib.mask[4 * (size_t)s + 1];
+        const uint64_t m2 = ib.mask[4 * (size_t)s + 2], m3 = ib.mask[4 * (size_t)s + 3];
 #pragma unroll
-    for (int j = 0; j < PL; j++) {
-        const int dz = q * PL + j;
-        const int z = i0[2] + dz - 1;
-        const R wz = w[2][0] * (dz == 0) + w[2][1] * (dz == 1) + w[2][2] * (dz == 2) + w[2][3] * (dz == 3);
+        for (int j = 0; j < PL; j++) {
+            const int dz = q * PL + j;
+            const int jz = d[2] + dz + 1;
+            const R wz = w[2][0] * (dz == 0) + w[2][1] * (dz == 1) + w[2][2] * (dz == 2) + w[2][3] * (dz == 3);
 #pragma unroll
-        for (int dy = 0; dy < 4; dy++) {
-            const int y = i0[1] + dy - 1;
-            lb[dy + 4 * j] = 0;
-            if (y < 0 || y >= ny || z < 0 || z >= nz) continue;
-            const int r = ib.rowid[ip.rowid_off + y + ny * z];
-            if (r < 0) continue;
-            const int x0 = p.rows[r].x0, len = p.rows[r].len, base = p.rows[r].off - x0;
-            lb[dy + 4 * j] = base;
-            const R wyz = w[1][dy] * wz;
+            for (int dy = 0; dy < 4; dy++) {
+                const int jy = d[1] + dy + 1;
+                const int base = lines[jy + 6 * jz];
+                lb[dy + 4 * j] = base;
+                const R wyz = w[1][dy] * wz;
 #pragma unroll
-            for (int dx = 0; dx < 4; dx++) {
-                const int x = i0[0] + dx - 1;
-                if (x < x0 || x >= x0 + len) continue;
-                const int c = base + x;
-                const uint32_t fl = p.flags[c];
-                if (!(fl & FL_ACTIVE)) continue;  // wall or boundary slot: no fluid, no force
-                if (!(fl & FL_BAND)) {
-                    out_of_band = true;
-                    continue;
+                for (int dx = 0; dx < 4; dx++) {
+                    const int bit = d[0] + dx + 1 + 6 * (jy + 6 * jz);
+                    const uint64_t word = bit < 64 ? m0 : bit < 128 ? m1 : bit < 192 ? m2 : m3;
+                    if (!((word >> (bit & 63)) & 1ull)) continue;  // wall or boundary slot: no fluid
+                    valid |= 1ull << (dx + 4 * (dy + 4 * j));
+                    const V v = vb[base + i0[0] + dx - 1];
+                    const R dd = w[0][dx] * wyz;
+                    vx += v.x * dd;
+                    vy += v.y * dd;
+                    vz += v.z * dd;
                 }
-                valid |= 1ull << (dx + 4 * (dy + 4 * j));
-                const V v = vb[c];
-                const R d = w[0][dx] * wyz;
-                vx += v.x * d;
-                vy += v.y * d;
-                vz += v.z * d;
             }
         }
     }

@@ -117,6 +117,13 @@ struct Layout {
     int64_t n_partial = 0;
     // immersed boundary
     std::vector<int32_t> band;          // compact cells flagged FL_BAND
+    // per wall node, around its reference cell i0 = floor(X0 - 0.5): compact
+    // index of x = 0 on the 36 lattice lines y = i0y - 2 .. +3, z = i0z - 2 .. +3
+    // (line jy + 6 jz), and a 216-bit mask of the fluid cells of that 6^3 box
+    // (bit jx + 6 (jy + 6 jz), x = i0x - 2 + jx), as 4 x 64-bit words
+    std::vector<int32_t> ib_lines;
+    std::vector<uint64_t> ib_mask;
+    std::vector<int32_t> ib_ref;        // i0 per node (3 ints)
     std::vector<double> ib_X0, ib_dA, ib_ks;
     std::vector<uint8_t> ib_pinned;
 };

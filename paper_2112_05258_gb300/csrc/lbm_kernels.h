@@ -63,6 +63,9 @@ struct IbKParams {
     const uint8_t *pinned;
     void *vband;                // unforced velocity at band cells, 4 x compute type per cell
     int threads_per_node;       // 1, 2 or 4 threads of the node kernel per wall node
+    const int32_t *lines;       // 36 per node: compact index of x = 0 on the support lines
+    const uint64_t *mask;       // 4 per node: fluid cells of the 6^3 box around the reference cell
+    const int32_t *ref;         // 3 per node: reference cell floor(X0 - 0.5)
 };
 
 // variants {min resident 256-thread blocks per SM, cells per thread}:

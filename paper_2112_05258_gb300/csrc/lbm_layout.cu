@@ -273,6 +273,29 @@ std::string build_layout(const lbm_config *cfg, Layout &L) {
             L.ib_pinned.push_back(d.ib_pinned[s]);
             int i0[3];
             for (int a = 0; a < 3; a++) i0[a] = (int)std::floor(d.ib_X0[3 * s + a] - 0.5);
+            for (int a = 0; a < 3; a++) L.ib_ref.push_back(i0[a]);
+            uint64_t mask[4] = {0, 0, 0, 0};
+            for (int jz = 0; jz < 6; jz++)
+                for (int jy = 0; jy < 6; jy++) {
+                    const int y = i0[1] - 2 + jy, z = i0[2] - 2 + jz;
+                    int32_t base = 0;
+                    if (y >= 0 && y < ny && z >= 0 && z < nz) {
+                        const int r = L.rowid[ip.rowid_off + y + ny * z];
+                        if (r >= 0) {
+                            const RowInfo &ri = L.rows[r];
+                            base = ri.off - ri.x0;
+                            for (int jx = 0; jx < 6; jx++) {
+                                const int x = i0[0] - 2 + jx;
+                                if (x < ri.x0 || x >= ri.x0 + ri.len) continue;
+                                if (d.node[x + (int64_t)nx * (y + (int64_t)ny * z)] != 0) continue;
+                                const int bit = jx + 6 * (jy + 6 * jz);
+                                mask[bit >> 6] |= 1ull << (bit & 63);
+                            }
+                        }
+                    }
+                    L.ib_lines.push_back(base);
+                }
+            for (int k = 0; k < 4; k++) L.ib_mask.push_back(mask[k]);
             for (int dz = -2; dz <= 3; dz++)
                 for (int dy = -2; dy <= 3; dy++)
                     for (int dx = -2; dx <= 3; dx++) {
