@@ -96,7 +96,6 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib) {
     const int s = gt / TPN, q = gt % TPN;
     if (s >= ib.n_nodes) return;  // the lanes of a node leave together
     const InstParam &ip = ib.inst[ib.node_inst[s]];
-    const int ny = ip.ny, nz = ip.nz;
     double X[3];
     int i0[3];
     R w[3][4];
