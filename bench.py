@@ -37,7 +37,9 @@ METRIC = "D3Q19 MLUPS & % HBM roofline; time-to-periodic-state vs plain FP32 at 
 FALLBACK_HBM_GBS = 6800.0
 BYTES_PER_CELL = {"f32": 152, "f16": 76, "bf16": 76, "f64": 304}
 PROFILE_MD = os.path.join(ROOT, "profiles", "stream_collide_tube_f32.md")
-KERNEL_SRC = os.path.join(ROOT, "paper_2112_05258_gb300", "csrc", "lbm_kernels.cu")
+# the sources the stream-collide kernel is compiled from
+KERNEL_SRC = [os.path.join(ROOT, "paper_2112_05258_gb300", "csrc", f)
+              for f in ("lbm_stream_collide.cu", "lbm_device.cuh")]
 
 
 def parse_args():
@@ -89,6 +91,13 @@ def measured_peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def kernel_source_sha256() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SRC:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()
+
+
 def profiled_traffic():
     """dram bytes per stream-collide launch from the committed ncu summary, if
     that summary was taken on the current kernel source (else None)."""
@@ -99,7 +108,7 @@ def profiled_traffic():
     m2 = re.search(r"dram_bytes_per_launch_full_size:\s*([0-9.eE+]+)", txt)
     if not (m1 and m2):
         return None
-    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    sha = kernel_source_sha256()
     return float(m2.group(1)) if sha == m1.group(1) else None
 
 

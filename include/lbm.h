@@ -62,9 +62,12 @@ typedef enum {
  *   VELOCITY: {omega}; profile = n_profile x {u_mean, c_re, c_im} in raster
  *             order of the boundary's nodes (n_profile must equal the node
  *             count); prescribed normal velocity u_mean + Re{c e^{i omega t}}.
- *   RCR:      {R_p, C, R_d, P_w0}   (Z_w = R_p, C_w = C, R_w = R_d)
- *   LV:       {period, P_la, N_S, P_v0}; elastance = period x {E, dE/dt} at
- *             integer steps (the C_v(t) = 1/E input of Algorithm 1)
+ *   RCR:      {R_p, C, R_d, P_w0[, order]}   (Z_w = R_p, C_w = C, R_w = R_d)
+ *   LV:       {period, P_la, N_S, P_v0[, order]}; elastance = period x {E, dE/dt}
+ *             at integer steps (the C_v(t) = 1/E input of Algorithm 1)
+ *             order (optional, default 1): 1 forward Euler, 2 Heun, 4 classical
+ *             Runge-Kutta, the boundary flow held over the step (the LV
+ *             elastance at half steps by cubic Hermite interpolation)
  *   PRESSURE: {p_gauge}                                                   */
 typedef struct {
     int kind;
@@ -168,6 +171,15 @@ lbm_status lbm_read_waveforms(lbm_handle *h, int inst, double *out, int64_t max_
  * position X, velocity V_s, force on the fluid F, interpolated V_f. */
 lbm_status lbm_read_ib(lbm_handle *h, int inst, double *X, double *Vs, double *F, double *Vf);
 lbm_status lbm_set_ib_state(lbm_handle *h, int inst, const double *X, const double *Vs);
+
+/* Wall shear stress (Section 3.2's WSS = mu dv_1/dx_3 at the fluid points next
+ * to the wall) at every fluid node of instance inst with a rigid-wall
+ * neighbour: the tangential part of the viscous traction sigma . n, with
+ * sigma = -(1 - 1/(2 tau)) [sum_i e_i e_i (f_i - f^eq_i) + (v b + b v)/2]
+ * from f(t_n) (lattice units, rho0 = 1) and n the unit normal into the
+ * fluid (normalised sum of e_i over the bounce-back directions).  Host
+ * output: 3 doubles per box node, box order (x fastest), zero elsewhere. */
+lbm_status lbm_wall_shear(lbm_handle *h, int inst, double *wss);
 
 /* Sets f_i(x, t_0) = f^eq_i(P, v) (Eq. feq) at every fluid node of instance
  * inst from host arrays of nx*ny*nz doubles (box order; non-fluid entries

@@ -64,6 +64,7 @@ def lib():
             L.orc_get_macros.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
             L.orc_get_force.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
             L.orc_get_0d.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
+            L.orc_wall_shear.argtypes = [ctypes.c_void_p, _dp]
             L.orc_wave_rows.restype = ctypes.c_long
             L.orc_wave_rows.argtypes = [ctypes.c_void_p]
             L.orc_get_waves.argtypes = [ctypes.c_void_p, _dp]
@@ -85,6 +86,11 @@ def lib():
             L.orc_lv_step.argtypes = [_dp, _dp, _dp, ctypes.c_long, ctypes.c_double,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_double, ctypes.POINTER(ctypes.c_int)]
+            L.orc_rcr_step_ord.restype = ctypes.c_double
+            L.orc_rcr_step_ord.argtypes = [_dp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, ctypes.c_int]
+            L.orc_lv_ode_ord.restype = ctypes.c_double
+            L.orc_lv_ode_ord.argtypes = [ctypes.c_double] * 6 + [ctypes.c_int]
             L.orc_phi.restype = ctypes.c_double
             L.orc_phi.argtypes = [ctypes.c_double]
             _lib = L
@@ -125,6 +131,16 @@ def rcr_step(Pw: float, Qout: float, Rp: float, C: float, Rd: float):
 
 def lv_ode(Pv: float, E: float, Edot: float, Qin: float) -> float:
     return lib().orc_lv_ode(Pv, E, Edot, Qin)
+
+
+def rcr_step_ord(Pw: float, Qout: float, Rp: float, C: float, Rd: float, order: int):
+    s = np.array([Pw], dtype=np.float64)
+    P = lib().orc_rcr_step_ord(_p(s), Qout, Rp, C, Rd, int(order))
+    return float(s[0]), P
+
+
+def lv_ode_ord(Pv, E0, D0, E1, D1, Qin, order):
+    return lib().orc_lv_ode_ord(Pv, E0, D0, E1, D1, Qin, int(order))
 
 
 def lv_step(Pv, valve_open, Td, n, E, Edot, Qu, Pbar_gauge, P_la):
@@ -216,6 +232,12 @@ class Oracle:
     def force(self):
         out = [np.empty(self.N) for _ in range(3)]
         lib().orc_get_force(self._h, *[_p(a) for a in out])
+        return out
+
+    def wall_shear(self) -> np.ndarray:
+        """(N, 3) tangential wall traction at the fluid cells next to a wall."""
+        out = np.empty((self.N, 3))
+        lib().orc_wall_shear(self._h, _p(out))
         return out
 
     def state_0d(self, k: int) -> np.ndarray:

@@ -164,6 +164,62 @@ double orc_lv_ode(double Pv, double E, double Edot, double Qin)
     return Pv - (1.0 / Cv) * (dCv * Pv + Qin);
 }
 
+/* Higher-order marching of the same ODEs (the paper allows "forward Euler or
+ * higher-order"), with the boundary flow held constant over the step:
+ * order 1 forward Euler, 2 Heun (RK2), 4 classical Runge-Kutta. */
+static double rcr_rhs(double Pw, double Qout, double C, double Rd) { return Qout / C - Pw / (Rd * C); }
+
+double orc_rcr_step_ord(double *Pw, double Qout, double Rp, double C, double Rd, int order)
+{
+    double P0 = *Pw, Pn;
+    if (order == 2) {
+        double k1 = rcr_rhs(P0, Qout, C, Rd);
+        double k2 = rcr_rhs(P0 + k1, Qout, C, Rd);
+        Pn = P0 + 0.5 * (k1 + k2);
+    } else if (order == 4) {
+        double k1 = rcr_rhs(P0, Qout, C, Rd);
+        double k2 = rcr_rhs(P0 + 0.5 * k1, Qout, C, Rd);
+        double k3 = rcr_rhs(P0 + 0.5 * k2, Qout, C, Rd);
+        double k4 = rcr_rhs(P0 + k3, Qout, C, Rd);
+        Pn = P0 + (k1 + 2.0 * k2 + 2.0 * k3 + k4) / 6.0;
+    } else {
+        return orc_rcr_step(Pw, Qout, Rp, C, Rd);
+    }
+    *Pw = Pn;
+    return Pn + Rp * Qout;
+}
+
+/* Elastance between table points n and n+1 at s in [0, 1]: cubic Hermite
+ * interpolation of (E, dE/dt) at both ends; returns E and writes dE/dt. */
+static double hermite_E(double E0, double D0, double E1, double D1, double s, double *dE)
+{
+    double s2 = s * s, s3 = s2 * s;
+    double h00 = 2 * s3 - 3 * s2 + 1, h10 = s3 - 2 * s2 + s, h01 = -2 * s3 + 3 * s2, h11 = s3 - s2;
+    double d00 = 6 * s2 - 6 * s, d10 = 3 * s2 - 4 * s + 1, d01 = -6 * s2 + 6 * s, d11 = 3 * s2 - 2 * s;
+    *dE = d00 * E0 + d10 * D0 + d01 * E1 + d11 * D1;
+    return h00 * E0 + h10 * D0 + h01 * E1 + h11 * D1;
+}
+
+/* Eq. LVE as dP_v/dt = (E'/E) P_v - E Q (C_v = 1/E), marched from t_n to
+ * t_{n+1} with table values (E0, D0) at t_n and (E1, D1) at t_{n+1}. */
+double orc_lv_ode_ord(double Pv, double E0, double D0, double E1, double D1, double Qin, int order)
+{
+    if (order == 2) {
+        double k1 = (D0 / E0) * Pv - E0 * Qin;
+        double k2 = (D1 / E1) * (Pv + k1) - E1 * Qin;
+        return Pv + 0.5 * (k1 + k2);
+    }
+    if (order == 4) {
+        double Dh, Eh = hermite_E(E0, D0, E1, D1, 0.5, &Dh);
+        double k1 = (D0 / E0) * Pv - E0 * Qin;
+        double k2 = (Dh / Eh) * (Pv + 0.5 * k1) - Eh * Qin;
+        double k3 = (Dh / Eh) * (Pv + 0.5 * k2) - Eh * Qin;
+        double k4 = (D1 / E1) * (Pv + k3) - E1 * Qin;
+        return Pv + (k1 + 2.0 * k2 + 2.0 * k3 + k4) / 6.0;
+    }
+    return orc_lv_ode(Pv, E0, D0, Qin);
+}
+
 /* One 0D step of the hybrid LV inlet (Sections 2.1.2, 2.2.1).
  * Inputs: current state, step index n (time t_n), Q_u(t_n), gauge mean
  * boundary pressure at t_n.  Readings:
@@ -173,12 +229,12 @@ double orc_lv_ode(double Pv, double E, double Edot, double Qin)
  *  - while closed the ventricle refills from an atrial pressure P_la through
  *    an ideal diode (P_v is held at P_la when it would fall below it);
  *  - T_d is t_n of the step at which Q_u < 0 was seen. */
-void orc_lv_step(double *Pv, double *valve_open, double *Td, long n,
-                 double E, double Edot, double Qu, double Pbar_gauge,
-                 double P_la, int *closed_now)
+void orc_lv_step_ord(double *Pv, double *valve_open, double *Td, long n,
+                     double E, double Edot, double E1, double Edot1, int order,
+                     double Qu, double Pbar_gauge, double P_la, int *closed_now)
 {
     double Qin = (*valve_open != 0.0) ? Qu : 0.0;
-    double Pn = orc_lv_ode(*Pv, E, Edot, Qin);
+    double Pn = orc_lv_ode_ord(*Pv, E, Edot, E1, Edot1, Qin, order);
     *closed_now = 0;
     if (*valve_open != 0.0) {
         if (Qu < 0.0) {
@@ -193,6 +249,13 @@ void orc_lv_step(double *Pv, double *valve_open, double *Td, long n,
             *valve_open = 1.0;
     }
     *Pv = Pn;
+}
+
+void orc_lv_step(double *Pv, double *valve_open, double *Td, long n,
+                 double E, double Edot, double Qu, double Pbar_gauge,
+                 double P_la, int *closed_now)
+{
+    orc_lv_step_ord(Pv, valve_open, Td, n, E, Edot, E, Edot, 1, Qu, Pbar_gauge, P_la, closed_now);
 }
 
 /* ---------------------------------------------------------------------- */
@@ -527,16 +590,18 @@ static void evolve_0d(orc_t *o)
         bc_t *b = &o->bc[k];
         double Pbar_g = b->Pbar - PREF;
         if (b->kind == BC_RCR) {
-            b->Pstar_gauge = orc_rcr_step(&b->Pw, -b->Qu, b->par[0], b->par[1], b->par[2]);
+            b->Pstar_gauge = orc_rcr_step_ord(&b->Pw, -b->Qu, b->par[0], b->par[1], b->par[2], (int)b->par[4]);
         } else if (b->kind == BC_PRESSURE) {
             b->Pstar_gauge = b->par[0];
         } else if (b->kind == BC_LV) {
             int T = b->period;
             double E = b->etab[2 * (n % T) + 0];
             double Edot = b->etab[2 * (n % T) + 1];
+            double E1 = b->etab[2 * ((n + 1) % T) + 0];
+            double Edot1 = b->etab[2 * ((n + 1) % T) + 1];
             int closed_now = 0;
-            orc_lv_step(&b->Pv, &b->valve_open, &b->Td, n, E, Edot, b->Qu, Pbar_g,
-                        b->par[1], &closed_now);
+            orc_lv_step_ord(&b->Pv, &b->valve_open, &b->Td, n, E, Edot, E1, Edot1, (int)b->par[4],
+                            b->Qu, Pbar_g, b->par[1], &closed_now);
             if (closed_now) {
                 for (long a = 0; a < b->n_xf; a++) {
                     long c = b->xf[a];
@@ -734,6 +799,64 @@ void orc_get_0d(void *h, int k, double *out)
         out[5] = b->Pv / b->etab[2 * (o->step % b->period)];
     out[6] = b->valve_open;
     out[7] = b->Td;
+}
+
+/* Wall shear stress at the fluid points next to a rigid wall (Section 3.2:
+ * WSS = mu dv_1/dx_3 there).  Reading: the viscous stress of the current f(t_n)
+ * from its non-equilibrium part, sigma = -(1 - 1/(2 tau)) [sum_i e_i e_i
+ * (f_i - f^eq_i(P, v)) + (v b + b v)/2] with v = j/rho0 + b/2 (Guo forcing);
+ * the wall normal n is the normalised sum of e_i over the directions whose
+ * pull source is a wall (pointing into the fluid); the output is the
+ * tangential traction sigma.n - (n.sigma.n) n, 3 values per box cell, zero
+ * away from walls.  The force density b is the one of the last step. */
+void orc_wall_shear(void *h, double *out)
+{
+    orc_t *o = (orc_t *)h;
+    compute_macros(o);
+    memset(out, 0, sizeof(double) * 3 * o->N);
+    for (long c = 0; c < o->N; c++) {
+        if (o->node[c] != N_FLUID)
+            continue;
+        int x = (int)(c % o->nx), y = (int)((c / o->nx) % o->ny), z = (int)(c / ((long)o->nx * o->ny));
+        double n[3] = {0, 0, 0};
+        int walls = 0;
+        for (int i = 1; i < NQ; i++) {
+            long src = nbr(o, x, y, z, -EX[i], -EY[i], -EZ[i]);
+            if (src < 0 || o->node[src] == N_WALL) {
+                n[0] += EX[i];
+                n[1] += EY[i];
+                n[2] += EZ[i];
+                walls++;
+            }
+        }
+        double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (walls == 0 || nn == 0.0)
+            continue;
+        for (int a = 0; a < 3; a++)
+            n[a] /= nn;
+        double b[3] = {o->bx[c], o->by[c], o->bz[c]};
+        double v[3] = {o->jx[c] / RHO0 + b[0] / (2 * RHO0), o->jy[c] / RHO0 + b[1] / (2 * RHO0),
+                       o->jz[c] / RHO0 + b[2] / (2 * RHO0)};
+        double feq[NQ];
+        orc_feq(o->P[c], v, feq);
+        double sig[3][3];
+        for (int a = 0; a < 3; a++)
+            for (int bb = 0; bb < 3; bb++) {
+                double pi = 0.0;
+                for (int i = 0; i < NQ; i++) {
+                    int e[3] = {EX[i], EY[i], EZ[i]};
+                    pi += e[a] * e[bb] * (o->f[i * o->N + c] - feq[i]);
+                }
+                sig[a][bb] = -(1.0 - 1.0 / (2.0 * o->tau)) * (pi + 0.5 * (v[a] * b[bb] + b[a] * v[bb]));
+            }
+        double t[3], tn = 0.0;
+        for (int a = 0; a < 3; a++) {
+            t[a] = sig[a][0] * n[0] + sig[a][1] * n[1] + sig[a][2] * n[2];
+            tn += t[a] * n[a];
+        }
+        for (int a = 0; a < 3; a++)
+            out[3 * c + a] = t[a] - tn * n[a];
+    }
 }
 
 long orc_wave_rows(void *h) { return ((orc_t *)h)->wave_rows; }

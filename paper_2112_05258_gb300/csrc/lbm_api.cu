@@ -144,6 +144,10 @@ lbm_status check_config(const lbm_config *cfg, std::string &why) {
             if (b.n_params < need[b.kind] || !b.params) return why = "too few boundary params", LBM_ERR_ARG;
             if (b.kind == LBM_BC_RCR && (!(b.params[1] > 0) || !(b.params[2] > 0)))
                 return why = "RCR needs C > 0 and R_d > 0", LBM_ERR_ARG;
+            if ((b.kind == LBM_BC_RCR || b.kind == LBM_BC_LV) && b.n_params >= 5) {
+                const double o = b.params[4];
+                if (!(o == 0 || o == 1 || o == 2 || o == 4)) return why = "0D scheme order must be 0, 1, 2 or 4", LBM_ERR_ARG;
+            }
             if (b.kind == LBM_BC_LV) {
                 if (b.period <= 0 || !b.elastance || (int)b.params[0] != b.period)
                     return why = "LV period and elastance table disagree", LBM_ERR_ARG;
@@ -425,6 +429,8 @@ lbm_status lbm_set_0d_params(lbm_handle *h, int inst, int bc, const double *p, i
     if (bp.kind == BC_RCR && (!(p[1] > 0) || !(p[2] > 0))) return fail(h, LBM_ERR_ARG, "RCR needs C, R_d > 0");
     if (bp.kind == BC_LV && ((int)p[0] != bp.period || !(p[2] > 0)))
         return fail(h, LBM_ERR_ARG, "LV period is fixed at creation; N_S > 0");
+    if ((bp.kind == BC_RCR || bp.kind == BC_LV) && np >= 5 && !(p[4] == 0 || p[4] == 1 || p[4] == 2 || p[4] == 4))
+        return fail(h, LBM_ERR_ARG, "0D scheme order must be 0, 1, 2 or 4");
     for (int k = 0; k < np; k++) bp.par[k] = p[k];
     CK(h, cudaSetDevice(h->device));
     CK(h, cudaStreamSynchronize(h->stream));
@@ -632,6 +638,25 @@ lbm_status lbm_get_kernel_time(lbm_handle *h, int64_t *launches, double *total_m
     h->ev_used = 0;
     *launches = h->timed_launches;
     *total_ms = h->timed_ms;
+    return LBM_OK;
+}
+
+lbm_status lbm_wall_shear(lbm_handle *h, int inst, double *wss) {
+    if (bad_inst(h, inst) || !wss) return fail(h, LBM_ERR_ARG, "bad instance or array");
+    CK(h, cudaSetDevice(h->device));
+    const Layout &L = h->L;
+    const int64_t c0 = L.inst_cell_begin[inst], c1 = L.inst_cell_end[inst];
+    const size_t M = (size_t)(c1 - c0);
+    if (!h->rd_mac) CK(h, dalloc(h, &h->rd_mac, 4 * (size_t)h->max_inst_cells));
+    CK(h, launch_wall_shear(h->prec, h->f[h->parity], h->kp, (int)c0, (int)c1, h->rd_mac, h->stream));
+    std::vector<double> tmp(3 * M);
+    CK(h, cudaMemcpyAsync(tmp.data(), h->rd_mac, 3 * M * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    const lbm_instance_desc &d = h->inst[inst];
+    const size_t nbox = (size_t)d.nx * d.ny * d.nz;
+    std::fill(wss, wss + 3 * nbox, 0.0);
+    for (size_t m = 0; m < M; m++)
+        for (int a = 0; a < 3; a++) wss[3 * (size_t)L.cell_box[c0 + m] + a] = tmp[a * M + m];
     return LBM_OK;
 }
 

@@ -10,26 +10,13 @@
 //                   integral and force F = alpha I + beta (V_f - V_s) on the
 //                   fluid, spreading of F delta dA with one vector atomic per
 //                   cell, spring update.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-#include <cuda_runtime.h>
-
-#include "lbm_kernels.h"
+#include "lbm_device.cuh"
 
 namespace lbm {
 
-template <class S> struct IbStorage;
-template <> struct IbStorage<float> { using R = float; static __device__ float ld(const float *p) { return __ldg(p); } };
-template <> struct IbStorage<double> { using R = double; static __device__ double ld(const double *p) { return __ldg(p); } };
-template <> struct IbStorage<__half> { using R = float; static __device__ float ld(const __half *p) { return __half2float(__ldg(p)); } };
-template <> struct IbStorage<__nv_bfloat16> {
-    using R = float;
-    static __device__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
-};
-
 template <class S>
 __global__ void k_band_moments(const S *__restrict__ fin, KParams p, IbKParams ib) {
-    using R = typename IbStorage<S>::R;
+    using R = typename Storage<S>::R;
     using V = typename Vec4<R>::T;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= ib.n_band) return;
@@ -45,7 +32,7 @@ __global__ void k_band_moments(const S *__restrict__ fin, KParams p, IbKParams i
         size_t idx;
         if (fl & (1u << i)) idx = (size_t)opp(i) * N + c;
         else idx = (size_t)i * N + (size_t)(p.rows[r].nb[nbk(i)] + x - cx(i));
-        const R fi = IbStorage<S>::ld(fin + idx);
+        const R fi = Storage<S>::ld(fin + idx);
         if (cx(i)) jx += cx(i) * fi;
         if (cy(i)) jy += cy(i) * fi;
         if (cz(i)) jz += cz(i) * fi;
@@ -89,7 +76,7 @@ __device__ __forceinline__ void vec_atomic_add(double4a *a, double4a v) {
 // compute the same penalty force; lane 0 writes the node state.
 template <class S, int TPN>
 __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib) {
-    using R = typename IbStorage<S>::R;
+    using R = typename Storage<S>::R;
     using V = typename Vec4<R>::T;
     constexpr int PL = 4 / TPN;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;

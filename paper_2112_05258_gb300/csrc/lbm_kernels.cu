@@ -1,13 +1,12 @@
-// Device kernels of the per-step hot path:
-//   k_stream_collide  fused pull-stream + halfway bounce-back + moments + BGK
-//                     collision with forcing (Eqs. fi, feq, f, rho, v), one
-//                     thread per stored cell of the compact row layout
+// Device kernels of the per-step hot path besides the fused stream-collide
+// (lbm_stream_collide.cu) and the immersed boundary (lbm_ib.cu):
 //   k_bc_reduce       deterministic FP64 partial sums of the boundary flow Q
 //                     and pressure over the first fluid layer of each 0D boundary
 //   k_bc_apply        the FP64 forward-Euler 0D step (Eqs. rightbc, rightQ,
 //                     LVE; valve switch and smoothing of Section 2.2.1) and
 //                     the ghost populations of Eq. Non-equilibrium3
 //   k_gather          read-out of f(t_n), P and j for the host
+//   k_wall_shear      wall shear stress at the fluid cells next to rigid walls
 //   k_init, k_init_eq inverse of the pull: lays out a given f(t_0), or the
 //                     equilibrium of given macroscopic fields
 //   k_cycle_change    cycle-to-cycle change of the 0D waveforms
@@ -17,143 +16,13 @@
 // steps is the post-collision field f*(t_n) with the ghost populations of
 // the 0D boundary nodes for t_{n+1} already in their slots, so one step is:
 // (immersed boundary) -> k_stream_collide -> k_bc_reduce -> k_bc_apply.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-#include <cuda_runtime.h>
-
-#include "lbm_kernels.h"
+#include "lbm_device.cuh"
 
 namespace lbm {
-
-template <class S> struct Storage;
-template <> struct Storage<float> {
-    using R = float;
-    static __device__ __forceinline__ float ld(const float *p) { return __ldg(p); }
-    static __device__ __forceinline__ void st(float *p, float v) { *p = v; }
-};
-template <> struct Storage<double> {
-    using R = double;
-    static __device__ __forceinline__ double ld(const double *p) { return __ldg(p); }
-    static __device__ __forceinline__ void st(double *p, double v) { *p = v; }
-};
-template <> struct Storage<__half> {
-    using R = float;
-    static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
-    static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
-};
-template <> struct Storage<__nv_bfloat16> {
-    using R = float;
-    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
-    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
-};
 
 __constant__ signed char c_ex[NQ] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
 __constant__ signed char c_ey[NQ] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
 __constant__ signed char c_ez[NQ] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
-
-// row of compact cell c: the row of its 32-cell chunk's first cell plus the
-// number of rows that begin within the chunk up to c's lane
-__device__ __forceinline__ int find_row(const KParams &p, int c) {
-    const int2 ch = __ldg(reinterpret_cast<const int2 *>(p.chunk_row) + (c >> 5));
-    const uint32_t upto = (2u << (c & 31)) - 1u;  // lanes 0..(c & 31)
-    return ch.x + __popc((uint32_t)ch.y & upto);
-}
-
-// ---------------------------------------------------------------------------
-// Fused stream-collide.  For each fluid cell x and direction i the pulled
-// population is f*_i(x - e_i) (or f*_opp(i)(x) when x - e_i is a rigid wall:
-// halfway bounce-back).  Then P = c_s^2 sum f, j = sum e f, v = j + b/2
-// (Eqs. rho, v), f^eq (Eq. feq), the forcing F_i (Eq. f) and BGK relaxation
-// (Eq. fi).  With s = f - w: sum f = 1 + sum s, j = sum e s, and
-// f^eq_i - w_i = w_i (sum s + 3 e.v + 9/2 (e.v)^2 - 3/2 v^2).
-// Occupancy request to ptxas (template parameter MINB: at least MINB resident
-// 256-thread blocks per SM).  MINB = 6 caps the kernel at 40 registers (75 %
-// occupancy) without spills; on the aorta it ran at 121 us per launch vs
-// 131 us at 48 registers (5 blocks) and 129 us at 32 registers (8 blocks,
-// with spills).  CPT > 1 gives each thread CPT independent cells, one grid
-// stride apart, whose loads are all issued before any of them is consumed
-// (more bytes in flight per thread at a lower occupancy).  The variants are
-// kept for the run-time autotuner.
-template <class S, int MINB, int CPT>
-__global__ void __launch_bounds__(256, MINB)
-    k_stream_collide(const S *__restrict__ fin, S *__restrict__ fout, KParams p) {
-    using R = typename Storage<S>::R;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int stride = gridDim.x * blockDim.x;
-    if (t == 0 && p.step) *p.step += 1;  // the step index t_n seen by the boundary kernels
-    // population i of cell k lives at fin[i * N + k]; 19 N < 2^31 is checked at creation
-    const uint32_t N = (uint32_t)p.n;
-    R f[CPT][NQ];
-    R om[CPT];
-    uint32_t fl[CPT];
-#pragma unroll
-    for (int u = 0; u < CPT; u++) {
-        const int c = t + u * stride;
-        fl[u] = c < p.n ? __ldg(&p.flags[c]) : 0u;
-        om[u] = R(0);
-        if (!(fl[u] & FL_ACTIVE)) continue;
-        const int r = find_row(p, c);
-        om[u] = (R)__ldg(&p.omega[__ldg(&p.rows[r].inst)]);
-        const int x = __ldg(&p.rows[r].x0) + (c - __ldg(&p.rows[r].off));
-        const int *nb = p.rows[r].nb;
-#pragma unroll
-        for (int i = 0; i < NQ; i++) {
-            uint32_t off;
-            if (i == 0) off = (uint32_t)c;
-            else if (fl[u] & (1u << i)) off = (uint32_t)opp(i) * N + (uint32_t)c;
-            else off = (uint32_t)i * N + (uint32_t)(__ldg(&nb[nbk(i)]) + x - cx(i));
-            f[u][i] = Storage<S>::ld(fin + off);
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < CPT; u++) {
-        if (!(fl[u] & FL_ACTIVE)) continue;
-        const int c = t + u * stride;
-        R sd = 0, jx = 0, jy = 0, jz = 0;
-#pragma unroll
-        for (int i = 0; i < NQ; i++) {
-            sd += f[u][i];
-            if (cx(i)) jx += cx(i) * f[u][i];
-            if (cy(i)) jy += cy(i) * f[u][i];
-            if (cz(i)) jz += cz(i) * f[u][i];
-        }
-        R bx = 0, by = 0, bz = 0;
-        const bool band = (fl[u] & FL_BAND) != 0;
-        if (band) {
-            const typename Vec4<R>::T bb = static_cast<const typename Vec4<R>::T *>(p.b)[c];
-            bx = bb.x;
-            by = bb.y;
-            bz = bb.z;
-        }
-        const R vx = jx + R(0.5) * bx, vy = jy + R(0.5) * by, vz = jz + R(0.5) * bz;
-        if (fl[u] & FL_XF) {
-            R *aux = static_cast<R *>(p.aux);
-            aux[c] = sd;
-            aux[N + c] = jx;
-            aux[2 * N + c] = jy;
-            aux[3 * N + c] = jz;
-        }
-        const R vv = vx * vx + vy * vy + vz * vz;
-        if (!(sd - sd == R(0)) || !(vv <= R(0.09))) atomicOr(p.status, 1u);
-
-        const R omega = om[u];
-        const R usq = R(1.5) * vv;
-        const R kf = R(1) - R(0.5) * omega;
-#pragma unroll
-        for (int i = 0; i < NQ; i++) {
-            const R w = (R)wgt(i);
-            const R eu = R(cx(i)) * vx + R(cy(i)) * vy + R(cz(i)) * vz;
-            const R seq = w * (sd + R(3) * eu + R(4.5) * eu * eu - usq);
-            R post = f[u][i] - omega * (f[u][i] - seq);
-            if (band) {
-                const R eb = R(cx(i)) * bx + R(cy(i)) * by + R(cz(i)) * bz;
-                const R vb = vx * bx + vy * by + vz * bz;
-                post += kf * w * (R(3) * (eb - vb) + R(9) * eu * eb);
-            }
-            Storage<S>::st(fout + ((uint32_t)i * N + (uint32_t)c), post);
-        }
-    }
-}
 
 // ---------------------------------------------------------------------------
 // 0D coupling.  One CTA per boundary.
@@ -215,8 +84,28 @@ __global__ void __launch_bounds__(BC_CHUNK) k_bc_reduce(KParams p, BcKParams q) 
     }
 }
 
+// Right-hand sides of the 0D ODEs with the boundary flow held over the step:
+// Windkessel chamber (Eqs. rightbc, rightQ with P eliminated) and ventricle
+// (Eq. LVE with C_v = 1/E: dP_v/dt = (E'/E) P_v - E Q).
+__device__ __forceinline__ double rcr_rate(double Pw, double Qout, double C, double Rd) {
+    return Qout / C - Pw / (Rd * C);
+}
+__device__ __forceinline__ double lv_rate(double Pv, double E, double Ed, double Q) { return (Ed / E) * Pv - E * Q; }
+
+// Elastance between table steps n and n+1 at s in [0, 1] by cubic Hermite
+// interpolation of the tabulated (E, dE/dt) at both ends.
+__device__ __forceinline__ void hermite_elastance(double E0, double D0, double E1, double D1, double s, double *E,
+                                                  double *D) {
+    const double s2 = s * s, s3 = s2 * s;
+    *E = (2 * s3 - 3 * s2 + 1) * E0 + (s3 - 2 * s2 + s) * D0 + (-2 * s3 + 3 * s2) * E1 + (s3 - s2) * D1;
+    *D = (6 * s2 - 6 * s) * E0 + (3 * s2 - 4 * s + 1) * D0 + (-6 * s2 + 6 * s) * E1 + (3 * s2 - 2 * s) * D1;
+}
+
 // The 0D step of one boundary from its state at t_n, given Q(t_n) and the
-// layer's pressure sum.  Returns the state at t_{n+1}.
+// layer's pressure sum.  Returns the state at t_{n+1}.  par[4] selects the
+// marching scheme: 0 or 1 forward Euler (the paper's), 2 Heun, 4 classical
+// Runge-Kutta (the paper allows higher order).  The forward-Euler forms are
+// written exactly as before so that the default trajectory is unchanged.
 __device__ BcState zero_d_step(const BcParam &P, const BcState &old, double Qt, double Psum, long long n,
                                const double *etab, int *ptype, int *closed, double *Smooth) {
     const double PREF = 1.0 / 3.0;
@@ -227,10 +116,21 @@ __device__ BcState zero_d_step(const BcParam &P, const BcState &old, double Qt, 
     *ptype = 1;
     *closed = 0;
     *Smooth = 0.0;
+    const int order = (int)P.par[4];
     if (P.kind == BC_RCR) {
-        // Eqs. rightbc/rightQ driven by the outflow -Q_u, forward Euler
-        const double Qout = -st.Qu;
-        const double Pw = old.Pw + (Qout / P.par[1] - old.Pw / (P.par[2] * P.par[1]));
+        // Eqs. rightbc/rightQ driven by the outflow -Q_u
+        const double Qout = -st.Qu, C = P.par[1], Rd = P.par[2], P0 = old.Pw;
+        double Pw;
+        if (order == 2) {
+            const double k1 = rcr_rate(P0, Qout, C, Rd), k2 = rcr_rate(P0 + k1, Qout, C, Rd);
+            Pw = P0 + 0.5 * (k1 + k2);
+        } else if (order == 4) {
+            const double k1 = rcr_rate(P0, Qout, C, Rd), k2 = rcr_rate(P0 + 0.5 * k1, Qout, C, Rd);
+            const double k3 = rcr_rate(P0 + 0.5 * k2, Qout, C, Rd), k4 = rcr_rate(P0 + k3, Qout, C, Rd);
+            Pw = P0 + (k1 + 2.0 * k2 + 2.0 * k3 + k4) / 6.0;
+        } else {
+            Pw = P0 + (Qout / C - P0 / (Rd * C));
+        }
         st.Pw = Pw;
         st.Pstar_gauge = Pw + P.par[0] * Qout;
     } else if (P.kind == BC_PRESSURE) {
@@ -241,8 +141,25 @@ __device__ BcState zero_d_step(const BcParam &P, const BcState &old, double Qt, 
         const double E = etab[2 * (P.etab_off + (int)(n % T))];
         const double Ed = etab[2 * (P.etab_off + (int)(n % T)) + 1];
         const double Qin = (old.valve_open != 0.0) ? st.Qu : 0.0;
-        const double Cv = 1.0 / E, dCv = -Ed / (E * E);
-        double Pv = old.Pv - (1.0 / Cv) * (dCv * old.Pv + Qin);
+        double Pv;
+        if (order == 2 || order == 4) {
+            const double E1 = etab[2 * (P.etab_off + (int)((n + 1) % T))];
+            const double D1 = etab[2 * (P.etab_off + (int)((n + 1) % T)) + 1];
+            const double P0 = old.Pv;
+            if (order == 2) {
+                const double k1 = lv_rate(P0, E, Ed, Qin), k2 = lv_rate(P0 + k1, E1, D1, Qin);
+                Pv = P0 + 0.5 * (k1 + k2);
+            } else {
+                double Eh, Dh;
+                hermite_elastance(E, Ed, E1, D1, 0.5, &Eh, &Dh);
+                const double k1 = lv_rate(P0, E, Ed, Qin), k2 = lv_rate(P0 + 0.5 * k1, Eh, Dh, Qin);
+                const double k3 = lv_rate(P0 + 0.5 * k2, Eh, Dh, Qin), k4 = lv_rate(P0 + k3, E1, D1, Qin);
+                Pv = P0 + (k1 + 2.0 * k2 + 2.0 * k3 + k4) / 6.0;
+            }
+        } else {
+            const double Cv = 1.0 / E, dCv = -Ed / (E * E);
+            Pv = old.Pv - (1.0 / Cv) * (dCv * old.Pv + Qin);
+        }
         if (old.valve_open != 0.0) {
             if (st.Qu < 0.0) {  // closure: the inflow has reversed
                 st.valve_open = 0.0;
@@ -415,6 +332,72 @@ __global__ void k_init(S *__restrict__ fout, KParams p, const double *__restrict
     }
 }
 
+// Wall shear stress at the fluid cells next to a rigid wall (the paper's
+// case-study observable, WSS = mu dv_1/dx_3 there): viscous stress of f(t_n)
+// from its non-equilibrium part, sigma = -(1 - 1/(2 tau)) [sum_i e_i e_i
+// (f_i - f^eq_i) + (v b + b v)/2], traction on the wall normal n (the
+// normalised sum of e_i over bounce-back directions, into the fluid), minus
+// its normal part.  Output 3 doubles per cell of [c0, c1) (zero elsewhere).
+template <class S>
+__global__ void k_wall_shear(const S *__restrict__ fin, KParams p, int c0, int c1, double *out3) {
+    const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= c1) return;
+    const size_t N = (size_t)p.n, M = (size_t)(c1 - c0), k = (size_t)(c - c0);
+    const uint32_t fl = p.flags[c];
+    out3[k] = out3[M + k] = out3[2 * M + k] = 0.0;
+    if (!(fl & FL_ACTIVE) || !(fl & FL_BBMASK)) return;
+    const int r = find_row(p, c);
+    const int x = p.rows[r].x0 + (c - p.rows[r].off);
+    double f[NQ], sum = 0, jx = 0, jy = 0, jz = 0, n[3] = {0, 0, 0};
+    for (int i = 0; i < NQ; i++) {
+        size_t idx;
+        if (i == 0) idx = c;
+        else if (fl & (1u << i)) idx = (size_t)opp(i) * N + c;
+        else idx = (size_t)i * N + (size_t)(p.rows[r].nb[nbk(i)] + x - cx(i));
+        f[i] = (double)Storage<S>::ld(fin + idx) + wgt(i);
+        sum += f[i];
+        jx += cx(i) * f[i];
+        jy += cy(i) * f[i];
+        jz += cz(i) * f[i];
+        if (i > 0 && (fl & (1u << i))) {
+            n[0] += cx(i);
+            n[1] += cy(i);
+            n[2] += cz(i);
+        }
+    }
+    const double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    if (nn == 0.0) return;
+    n[0] /= nn;
+    n[1] /= nn;
+    n[2] /= nn;
+    double b[3] = {0, 0, 0};
+    if (fl & FL_BAND) {
+        using R = typename Storage<S>::R;
+        const typename Vec4<R>::T bb = static_cast<const typename Vec4<R>::T *>(p.b)[c];
+        b[0] = bb.x;
+        b[1] = bb.y;
+        b[2] = bb.z;
+    }
+    const double v[3] = {jx + 0.5 * b[0], jy + 0.5 * b[1], jz + 0.5 * b[2]};
+    const double P = sum / 3.0, usq = 1.5 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    double pi[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    for (int i = 0; i < NQ; i++) {
+        const double e[3] = {(double)cx(i), (double)cy(i), (double)cz(i)};
+        const double eu = e[0] * v[0] + e[1] * v[1] + e[2] * v[2];
+        const double fneq = f[i] - wgt(i) * (3.0 * P + 3.0 * eu + 4.5 * eu * eu - usq);
+        for (int a = 0; a < 3; a++)
+            for (int q = 0; q < 3; q++) pi[a][q] += e[a] * e[q] * fneq;
+    }
+    const double kf = -(1.0 - 0.5 * p.omega[p.rows[r].inst]);
+    double t[3], tn = 0.0;
+    for (int a = 0; a < 3; a++) {
+        t[a] = 0.0;
+        for (int q = 0; q < 3; q++) t[a] += kf * (pi[a][q] + 0.5 * (v[a] * b[q] + b[a] * v[q])) * n[q];
+        tn += t[a] * n[a];
+    }
+    for (int a = 0; a < 3; a++) out3[a * M + k] = t[a] - tn * n[a];
+}
+
 // Equilibrium initialisation: f_i(x, t_0) = f^eq_i(P, v) (Eq. feq) from the
 // macroscopic fields of the fluid cells of [c0, c1) (4 x M doubles: P, vx,
 // vy, vz), laid out by the inverse of the pull like k_init.
@@ -483,47 +466,6 @@ __global__ void k_cycle_change(BcKParams q, const int *bc_first, const int *n_bc
 // ---------------------------------------------------------------------------
 // launchers
 
-template <class S> static S *as(void *p) { return static_cast<S *>(p); }
-
-#define DISPATCH(prec, CALL)                                   \
-    switch (prec) {                                            \
-    case 0: { using S = float; CALL; } break;                  \
-    case 1: { using S = __half; CALL; } break;                 \
-    case 2: { using S = __nv_bfloat16; CALL; } break;          \
-    default: { using S = double; CALL; } break;                \
-    }
-
-// variants: {min blocks per SM, cells per thread}
-static const int kVariants[SC_VARIANTS][2] = {{6, 1}, {8, 1}, {5, 1}, {4, 2}, {3, 2}};
-
-int stream_collide_min_blocks(int variant) { return kVariants[variant][0]; }
-int stream_collide_cells_per_thread(int variant) { return kVariants[variant][1]; }
-
-cudaError_t launch_stream_collide(int prec, const void *fin, void *fout, const KParams &p, int block,
-                                  int variant, cudaStream_t s) {
-    if (p.n == 0) return cudaSuccess;
-    const int cpt = kVariants[variant][1];
-    const int grid = (int)((p.n + (long long)block * cpt - 1) / ((long long)block * cpt));
-    switch (variant) {
-    case 1:
-        DISPATCH(prec, (k_stream_collide<S, 8, 1><<<grid, block, 0, s>>>(static_cast<const S *>(fin), as<S>(fout), p)));
-        break;
-    case 2:
-        DISPATCH(prec, (k_stream_collide<S, 5, 1><<<grid, block, 0, s>>>(static_cast<const S *>(fin), as<S>(fout), p)));
-        break;
-    case 3:
-        DISPATCH(prec, (k_stream_collide<S, 4, 2><<<grid, block, 0, s>>>(static_cast<const S *>(fin), as<S>(fout), p)));
-        break;
-    case 4:
-        DISPATCH(prec, (k_stream_collide<S, 3, 2><<<grid, block, 0, s>>>(static_cast<const S *>(fin), as<S>(fout), p)));
-        break;
-    default:
-        DISPATCH(prec, (k_stream_collide<S, 6, 1><<<grid, block, 0, s>>>(static_cast<const S *>(fin), as<S>(fout), p)));
-        break;
-    }
-    return cudaGetLastError();
-}
-
 cudaError_t launch_boundary(int prec, void *f, const KParams &p, const BcKParams &q, cudaStream_t s) {
     if (q.n_bc_total == 0) return cudaSuccess;
     if (prec == 3) k_bc_reduce<double><<<q.n_red_blocks, BC_CHUNK, 0, s>>>(p, q);
@@ -538,6 +480,15 @@ cudaError_t launch_gather(int prec, const void *fin, const KParams &p, int c0, i
     const int grid = (c1 - c0 + block - 1) / block;
     if (grid == 0) return cudaSuccess;
     DISPATCH(prec, (k_gather<S><<<grid, block, 0, s>>>(static_cast<const S *>(fin), p, c0, c1, f19, mac4)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wall_shear(int prec, const void *fin, const KParams &p, int c0, int c1, double *out3,
+                              cudaStream_t s) {
+    const int block = 128;
+    const int grid = (c1 - c0 + block - 1) / block;
+    if (grid == 0) return cudaSuccess;
+    DISPATCH(prec, (k_wall_shear<S><<<grid, block, 0, s>>>(static_cast<const S *>(fin), p, c0, c1, out3)));
     return cudaGetLastError();
 }
 

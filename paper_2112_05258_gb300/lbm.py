@@ -62,7 +62,8 @@ EXPORTS = ["lbm_create", "lbm_set_0d_params", "lbm_init_populations", "lbm_step"
            "lbm_read_fields", "lbm_read_populations", "lbm_read_0d_state", "lbm_read_waveforms",
            "lbm_read_ib", "lbm_set_ib_state", "lbm_set_kernel_timing", "lbm_get_kernel_time",
            "lbm_get_info", "lbm_last_error", "lbm_destroy", "lbm_boundary_flux_noalloc",
-           "lbm_init_equilibrium", "lbm_set_0d_state", "lbm_cycle_change", "lbm_autotune"]
+           "lbm_init_equilibrium", "lbm_set_0d_state", "lbm_cycle_change", "lbm_autotune",
+           "lbm_wall_shear"]
 
 _lib = None
 
@@ -97,6 +98,7 @@ def load(path: Optional[str] = None):
     L.lbm_destroy.argtypes = [H]
     L.lbm_destroy.restype = None
     L.lbm_init_equilibrium.argtypes = [H, ctypes.c_int, _dp, _dp, _dp, _dp]
+    L.lbm_wall_shear.argtypes = [H, ctypes.c_int, _dp]
     L.lbm_set_0d_state.argtypes = [H, ctypes.c_int, ctypes.c_int, _dp]
     L.lbm_cycle_change.argtypes = [H, ctypes.POINTER(ctypes.c_int64), _dp]
     L.lbm_autotune.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -268,6 +270,13 @@ class Lattice:
         ms = ctypes.c_double()
         self._ck(load().lbm_get_kernel_time(self._h, ctypes.byref(n), ctypes.byref(ms)))
         return n.value, ms.value
+
+    def wall_shear(self, inst: int = 0) -> np.ndarray:
+        """(nx*ny*nz, 3) tangential wall traction next to rigid walls (box order)."""
+        nx, ny, nz = self.shapes[inst]
+        out = np.empty((nx * ny * nz, 3))
+        self._ck(load().lbm_wall_shear(self._h, inst, _p(out)))
+        return out
 
     def init_equilibrium(self, inst: int, P, vx, vy, vz):
         arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in (P, vx, vy, vz)]

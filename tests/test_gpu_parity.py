@@ -83,15 +83,28 @@ def test_f64_pressure_tube(Lattice):
     assert_same(lat, o, inst)
 
 
-def test_f64_lv_hybrid_inlet(Lattice):
+@pytest.mark.parametrize("order", [1, 2, 4])
+def test_f64_lv_hybrid_inlet(Lattice, order):
     # several beats: the valve opens and closes, T_d and the smoothed closure
-    # velocity are exercised
+    # velocity are exercised; both 0D models marched at the given order
     inst = configs.lv_tube(period=600)
+    for b in inst.boundaries:
+        b.params = list(b.params[:4]) + [float(order)]
     lat = run_gpu(Lattice, inst, 1500)
     o = run_oracle(inst, 1500)
     w = o.waves()
     assert (np.diff(w[:, 4]) < 0).sum() >= 2        # at least two closures seen
     assert_same(lat, o, inst, atol_f=1e-11, atol_w=1e-11)
+    if order == 1:
+        assert_same_wss(lat, o, inst, 1e-12)
+
+
+def assert_same_wss(lat, o, inst, atol):
+    wg, wo = lat.wall_shear(0), o.wall_shear()
+    at = np.abs(wo).sum(axis=1) > 0
+    assert at.sum() > 0
+    assert np.array_equal(at, np.abs(wg).sum(axis=1) > 0)
+    assert np.abs(wg - wo).max() < atol
 
 
 def test_f64_immersed_boundary(Lattice):
@@ -102,6 +115,16 @@ def test_f64_immersed_boundary(Lattice):
     n = inst.ib.n
     for a, b in zip(lat.ib_state(0, n), o.ib_state()):
         assert np.abs(a - b).max() < 1e-12
+    assert_same_wss(lat, o, inst, 1e-12)        # band cells carry b in sigma
+
+
+def test_f32_wall_shear_rigid_tube(Lattice):
+    inst = configs.rigid_tube(16, 16, 24, radius=5.0, period=200)
+    lat = run_gpu(Lattice, inst, 400, prec="f32")
+    o = run_oracle(inst, 400)
+    wg, wo = lat.wall_shear(0), o.wall_shear()
+    at = np.abs(wo).sum(axis=1) > 0
+    assert np.abs(wg[at] - wo[at]).max() < 1e-3 * np.abs(wo).max() + 1e-9
 
 
 def _wave_rel_err(wg, wo, nbc):

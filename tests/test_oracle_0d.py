@@ -179,3 +179,66 @@ def test_closed_loop_pv_loop_periodic():
         errs.append(abs((vo - vc) - fl2) / fl2)
     assert errs[0] < 0.12
     assert 1.8 < errs[0] / errs[1] < 2.3 and 1.8 < errs[1] / errs[2] < 2.3, errs
+
+
+# ---- higher-order marching (Heun RK2, classical RK4) ----------------------
+
+@pytest.mark.parametrize("order", [2, 4])
+def test_rcr_higher_order_stability_polynomial(order):
+    # Q = 0: one step multiplies P_w by the method's stability polynomial
+    # R(z) at z = -dt/(R_d C): 1 + z + z^2/2 (RK2), + z^3/6 + z^4/24 (RK4)
+    z = -1.0 / (RD * C)
+    R = 1 + z + z * z / 2 + ((z ** 3 / 6 + z ** 4 / 24) if order == 4 else 0.0)
+    Pw = 0.01
+    for n in range(1, 301):
+        Pw, P = oracle.rcr_step_ord(Pw, 0.0, RP, C, RD, order)
+    assert Pw == pytest.approx(0.01 * R ** 300, rel=1e-12)
+
+
+@pytest.mark.parametrize("order,ratio", [(1, 2.0), (2, 4.0), (4, 16.0)])
+def test_rcr_convergence_order(order, ratio):
+    # sinusoidal outflow over one period of fixed length, resolved with M
+    # steps (C scaled with M so the time constant stays 0.2 of the period);
+    # error against the exact solution of the linear ODE with the input held
+    # piecewise constant, e^{-h/tau}-recursion, shrinks by 2^order per halving
+    errs = []
+    for M in (200, 400, 800):
+        Cm = 200.0 * M / 1000.0
+        Pw_num = Pw_ex = 0.0
+        a = math.exp(-1.0 / (RD * Cm))
+        for n in range(M):
+            q = 0.01 * math.cos(2 * math.pi * n / M)
+            Pw_num, _ = oracle.rcr_step_ord(Pw_num, q, RP, Cm, RD, order)
+            Pw_ex = a * Pw_ex + RD * q * (1 - a)     # exact over a step with q held
+        errs.append(abs(Pw_num - Pw_ex))
+    r = errs[0] / errs[1], errs[1] / errs[2]
+    assert all(0.8 * ratio < x < 1.25 * ratio for x in r), (errs, r)
+
+
+@pytest.mark.parametrize("order,ratio", [(1, 2.0), (2, 4.0), (4, 16.0)])
+def test_lv_invariant_higher_order(order, ratio):
+    # Q = 0 keeps C_v P_v = P_v / E constant; with a smooth elastance
+    # E(t) = a (1 + sin(2 pi t / T) / 2) the drift over 0.3 of a beat falls by
+    # 2^order per halving of dt (the double-Hill curve is not smooth at the
+    # beat start, t^1.32, so it would cap the observed order)
+    drifts = []
+    for T in (100, 200, 400):
+        n = np.arange(T + 1)
+        E = 1e-3 * (1 + 0.5 * np.sin(2 * np.pi * n / T))
+        D = 1e-3 * 0.5 * (2 * np.pi / T) * np.cos(2 * np.pi * n / T)
+        Pv = 1e-3
+        v0 = Pv / E[0]
+        m = int(round(0.3 * T))
+        for k in range(m):
+            Pv = oracle.lv_ode_ord(Pv, E[k], D[k], E[k + 1], D[k + 1], 0.0, order)
+        drifts.append(abs(Pv / E[m] - v0) / v0)
+    r = drifts[0] / drifts[1], drifts[1] / drifts[2]
+    assert all(0.8 * ratio < x < 1.25 * ratio for x in r), (drifts, r)
+
+
+def test_lv_higher_order_exact_for_constant_elastance():
+    for order in (2, 4):
+        Pv = 0.003
+        for _ in range(100):
+            Pv = oracle.lv_ode_ord(Pv, 2e-3, 0.0, 2e-3, 0.0, 0.01, order)
+        assert Pv == pytest.approx(0.003 - 100 * 2e-3 * 0.01, rel=1e-12)

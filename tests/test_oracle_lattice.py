@@ -239,3 +239,47 @@ def test_lv_inlet_hybrid_switching_in_lattice():
     n_s = int(inst.boundaries[0].params[2])
     c = closes[closes >= 3 * T][0]
     assert np.abs(w[c + n_s + 5: c + n_s + 50, 1]).max() < 0.05 * Qin.max()
+
+
+@pytest.mark.parametrize("tau", [TAU_MAGIC, 0.8])
+def test_wall_shear_channel(tau):
+    # steady channel flow: the tangential traction at the first fluid node
+    # equals rho nu du/dy there, in the flow direction at both walls; at the
+    # magic tau the discrete profile is the analytic parabola, so the value
+    # is g (H - 1) / 2 (H = ny - 2); elsewhere it is the slope of the
+    # discrete parabola fitted to the node velocities
+    ny, g = 12, 1e-6
+    node = geometry.plates_channel(1, ny, 1)
+    o = oracle.Oracle(Instance(node=node, tau=tau), periodic=1 | 4)
+    o.set_body_force([g, 0, 0])
+    o.step(40000)
+    w = o.wall_shear().reshape(ny, 3)
+    u = o.macros()[1].reshape(ny) + g / 2
+    y = np.arange(ny) + 0.5
+    c = np.polyfit(y[1:-1], u[1:-1], 2)
+    slope = np.polyval(np.polyder(c), 1.5)
+    nu = _nu(tau)
+    assert w[1, 0] == pytest.approx(nu * slope, rel=1e-8)
+    assert w[ny - 2, 0] == pytest.approx(w[1, 0], rel=1e-10)         # both walls, along +x
+    assert np.abs(w[1, 1:]).max() < 1e-18 and np.abs(w[2:ny - 2]).max() == 0.0
+    if tau == TAU_MAGIC:
+        assert w[1, 0] == pytest.approx(g * (ny - 3) / 2, rel=1e-9)
+
+
+def test_wall_shear_tube_direction_and_balance():
+    # periodic tube with axial force: the wall traction points along +z and
+    # its total over the wall cells balances the body force on the fluid to
+    # within the staircase error
+    R, g = 6, 1e-6
+    n = 2 * R + 4
+    node = geometry.periodic_tube(n, n, 1, R)
+    o = oracle.Oracle(Instance(node=node, tau=TAU_MAGIC), periodic=4)
+    o.set_body_force([0, 0, g])
+    o.step(int(6 * R * R / _nu(TAU_MAGIC)))
+    w = o.wall_shear()
+    at = np.abs(w).sum(axis=1) > 0
+    assert at.sum() > 0 and (w[at, 2] > 0).all()
+    assert np.abs(w[at, :2]).max() < 0.05 * w[at, 2].max()
+    perimeter = 2 * np.pi * R
+    mean_wss = g * (node == 0).sum() / perimeter      # force balance per unit length
+    assert w[at, 2].mean() == pytest.approx(mean_wss, rel=0.25)

@@ -41,9 +41,10 @@ class Boundary:
     * BC_VELOCITY: ``[omega]``; ``profile`` is ``(n_nodes, 3)`` float64 with
       columns ``u_mean, c_re, c_im`` in raster order of the boundary's nodes;
       the prescribed normal velocity is ``u_mean + Re{(c_re + i c_im) e^{i omega t}}``.
-    * BC_RCR: ``[R_p, C, R_d, P_w0]`` (characteristic impedance, compliance,
-      peripheral resistance, initial chamber pressure; gauge units).
-    * BC_LV: ``[period_steps, P_la, N_S, P_v0]``; ``elastance`` is a
+    * BC_RCR: ``[R_p, C, R_d, P_w0(, order)]`` (characteristic impedance,
+      compliance, peripheral resistance, initial chamber pressure; gauge
+      units; optional marching order 1, 2 or 4).
+    * BC_LV: ``[period_steps, P_la, N_S, P_v0(, order)]``; ``elastance`` is a
       ``(period_steps, 2)`` float64 table of ``E(t)`` and ``dE/dt`` at
       integer steps ``t mod period``.
     * BC_PRESSURE: ``[p_gauge]``.
