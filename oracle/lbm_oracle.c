@@ -493,13 +493,37 @@ static long support_cell(const orc_t *o, int ix, int iy, int iz)
 
 /* Sub-step 2: penalty force (Eq. LagForce) from the interpolated velocity
  * (Eq. interpolation) and spreading to the lattice (Eq. EulForce).
- * Readings: the interpolated velocity is the unforced j/rho0 of f(t_n); the
+ * Readings: the interpolated field is the fluid velocity of Eq. v,
+ * j/rho0 + b/(2 rho0), formed with the force density b still held from the
+ * previous step (the new b depends on V_f, so it cannot enter V_f); the
  * integral is updated before B is formed; the force on the fluid is
  * F = alpha I + beta (V_f - V_s) with alpha, beta < 0 and is spread with a
  * plus sign (the wall receives -F), which makes the penalty a feedback that
- * drives V_f towards V_s. */
+ * drives V_f towards V_s.  All nodes interpolate before any node spreads. */
 static void ib_force(orc_t *o)
 {
+    for (long s = 0; s < o->ns; s++) {
+        double *X = &o->X[3 * s];
+        int i0[3];
+        for (int a = 0; a < 3; a++)
+            i0[a] = (int)floor(X[a] - 0.5);
+        double Vf[3] = {0, 0, 0};
+        for (int dz = -1; dz <= 2; dz++)
+            for (int dy = -1; dy <= 2; dy++)
+                for (int dx = -1; dx <= 2; dx++) {
+                    int ix = i0[0] + dx, iy = i0[1] + dy, iz = i0[2] + dz;
+                    double d = orc_phi(ix + 0.5 - X[0]) * orc_phi(iy + 0.5 - X[1]) *
+                               orc_phi(iz + 0.5 - X[2]);
+                    long c = support_cell(o, ix, iy, iz);
+                    if (c < 0 || o->node[c] != N_FLUID)
+                        continue;
+                    Vf[0] += (o->jx[c] + 0.5 * o->bx[c]) / RHO0 * d;
+                    Vf[1] += (o->jy[c] + 0.5 * o->by[c]) / RHO0 * d;
+                    Vf[2] += (o->jz[c] + 0.5 * o->bz[c]) / RHO0 * d;
+                }
+        for (int a = 0; a < 3; a++)
+            o->Vf[3 * s + a] = Vf[a];
+    }
     for (long c = 0; c < o->N; c++) {
         int fl = o->node[c] == N_FLUID;
         o->bx[c] = fl ? o->g[0] : 0.0;
@@ -511,24 +535,8 @@ static void ib_force(orc_t *o)
         int i0[3];
         for (int a = 0; a < 3; a++)
             i0[a] = (int)floor(X[a] - 0.5);
-        /* interpolation */
-        double Vf[3] = {0, 0, 0};
-        for (int dz = -1; dz <= 2; dz++)
-            for (int dy = -1; dy <= 2; dy++)
-                for (int dx = -1; dx <= 2; dx++) {
-                    int ix = i0[0] + dx, iy = i0[1] + dy, iz = i0[2] + dz;
-                    double d = orc_phi(ix + 0.5 - X[0]) * orc_phi(iy + 0.5 - X[1]) *
-                               orc_phi(iz + 0.5 - X[2]);
-                    long c = support_cell(o, ix, iy, iz);
-                    if (c < 0 || o->node[c] != N_FLUID)
-                        continue;
-                    Vf[0] += o->jx[c] / RHO0 * d;
-                    Vf[1] += o->jy[c] / RHO0 * d;
-                    Vf[2] += o->jz[c] / RHO0 * d;
-                }
         for (int a = 0; a < 3; a++) {
-            o->Vf[3 * s + a] = Vf[a];
-            double dv = Vf[a] - o->Vs[3 * s + a];
+            double dv = o->Vf[3 * s + a] - o->Vs[3 * s + a];
             o->I[3 * s + a] += dv;
             o->F[3 * s + a] = o->alpha * o->I[3 * s + a] + o->beta * dv;
         }

@@ -2,9 +2,10 @@
 // (Section 2.3.2, Eqs. LagForce, interpolation, EulForce) and the wall-node
 // update (linear springs to the reference position, symplectic Euler).
 //
-//   k_band_moments  unforced velocity j/rho0 of f(t_n) at every band cell
-//                   (the cells within reach of a wall node's kernel support)
-//                   and b = 0 there; both as one 4-vector per cell
+//   k_band_moments  fluid velocity j/rho0 + b/2 of f(t_n) at every band cell
+//                   (the cells within reach of a wall node's kernel support),
+//                   b being the force density of the previous step, and then
+//                   b = 0 there; both as one 4-vector per cell
 //   k_ib_nodes      1, 2 or 4 threads per wall node: gather V_f over the 64
 //                   support cells of the 4-point cosine delta, penalty
 //                   integral and force F = alpha I + beta (V_f - V_s) on the
@@ -37,15 +38,19 @@ __global__ void k_band_moments(const S *__restrict__ fin, KParams p, IbKParams i
         if (cy(i)) jy += cy(i) * fi;
         if (cz(i)) jz += cz(i) * fi;
     }
+    // fluid velocity of Eq. v with the force density of the previous step,
+    // which is then cleared for this step's spreading
+    V *b = static_cast<V *>(const_cast<void *>(p.b));
+    const V bo = b[c];
     V v;
-    v.x = jx;
-    v.y = jy;
-    v.z = jz;
+    v.x = jx + R(0.5) * bo.x;
+    v.y = jy + R(0.5) * bo.y;
+    v.z = jz + R(0.5) * bo.z;
     v.w = 0;
     static_cast<V *>(ib.vband)[c] = v;
     V z;
     z.x = z.y = z.z = z.w = 0;
-    static_cast<V *>(const_cast<void *>(p.b))[c] = z;
+    b[c] = z;
 }
 
 // Weights of the 4-point cosine delta phi(r) = (1 + cos(pi r / 2)) / 4 at the

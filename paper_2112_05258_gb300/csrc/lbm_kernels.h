@@ -61,7 +61,7 @@ struct IbKParams {
     double *X, *Vs, *I, *F, *Vf;  // 3 per node
     const double *X0, *dA, *ks;
     const uint8_t *pinned;
-    void *vband;                // unforced velocity at band cells, 4 x compute type per cell
+    void *vband;                // fluid velocity j + b/2 (previous step's b) at band cells, 4 x compute type per cell
     int threads_per_node;       // 1, 2 or 4 threads of the node kernel per wall node
     const int32_t *lines;       // 36 per node: compact index of x = 0 on the support lines
     const uint64_t *mask;       // 4 per node: fluid cells of the 6^3 box around the reference cell
