@@ -34,6 +34,9 @@
 extern "C" {
 #endif
 
+/* largest filament (SGFD wall solid) in nodes */
+#define LBM_MAX_FILAMENT_NODES 3072
+
 typedef enum {
     LBM_OK = 0,
     LBM_ERR_ARG = -1,      /* invalid argument; nothing was enqueued */
@@ -98,6 +101,20 @@ typedef struct {
     const uint8_t *ib_pinned; /* n_ib, 1 = held at X0 */
     double ib_alpha, ib_beta; /* penalty gains, both < 0 */
     double ib_ms;             /* wall mass per area */
+    /* Optional filaments over the wall nodes (the SGFD solid of Section
+     * 2.3.2, Eqs. tension, 2nd order, bending): filament k is the next
+     * ib_fil_count[k] entries of ib_fil_nodes (wall-node indices of this
+     * instance in arc-length order, 3 .. 3072 nodes, each node in at most
+     * one filament) with ib_fil_par[3k .. 3k+2] = (ds, Eh, EI): reference
+     * node spacing > 0, stretching and bending stiffness >= 0 (per unit
+     * width).  Both end nodes must be pinned.  Each interior node adds the
+     * filament's tension and bending force (simply supported ends) to its
+     * spring; the update is the central difference in time.  Host arrays,
+     * copied; ib_n_fil = 0 for none. */
+    int64_t ib_n_fil;
+    const int64_t *ib_fil_count;
+    const int64_t *ib_fil_nodes;
+    const double *ib_fil_par;
 } lbm_instance_desc;
 
 typedef struct {
@@ -109,7 +126,7 @@ typedef struct {
     int graph_steps;   /* steps per captured CUDA graph (even, >= 2); 0 = 64 */
     int wave_capacity; /* waveform ring-buffer length in steps; 0 = 8192 */
     int block_size;    /* threads per block of the stream-collide kernel, multiple of 32 in [32, 256]; 0 = 128 */
-    int ib_threads_per_node; /* threads of the immersed-boundary node kernel per wall node: 1, 2 or 4; 0 = 1 */
+    int ib_threads_per_node; /* threads of the immersed-boundary node kernel per wall node: 1, 2 or 4; 0 = 2 */
 } lbm_config;
 
 typedef struct lbm_handle lbm_handle;
@@ -126,6 +143,20 @@ typedef struct {
     int precision;
     int bytes_per_population;
 } lbm_info_t;
+
+/* Sizes of the layout lbm_create would build (see lbm_check_config). */
+typedef struct {
+    int64_t fluid_cells, stored_cells, box_cells, band_cells, links;
+    int64_t ib_nodes, filaments;
+} lbm_layout_stats;
+
+/* Host only (no CUDA call, no GPU needed): validates cfg as lbm_create does
+ * and builds the compact row layout and the boundary and immersed-boundary
+ * tables, including the layout's self-check (every population pull
+ * resolved to the right stored cell).  stats may be NULL.  On failure returns LBM_ERR_ARG
+ * and writes the reason to why (NUL-terminated, at most why_len bytes;
+ * why may be NULL). */
+lbm_status lbm_check_config(const lbm_config *cfg, lbm_layout_stats *stats, char *why, int why_len);
 
 /* Builds the compact row layout of every instance, copies inputs, and
  * initialises the fluid at rest (f_i = w_i, P = P_ref, v = 0; Section 2.3.2)

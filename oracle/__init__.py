@@ -27,6 +27,7 @@ _lock = threading.Lock()
 _lib = None
 
 _dp = ctypes.POINTER(ctypes.c_double)
+_lp = ctypes.POINTER(ctypes.c_long)
 _u8p = ctypes.POINTER(ctypes.c_uint8)
 
 
@@ -57,6 +58,9 @@ def lib():
             L.orc_set_ib.argtypes = [ctypes.c_void_p, ctypes.c_long, _dp, _dp, _dp, _u8p,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_double]
             L.orc_set_ib_state.argtypes = [ctypes.c_void_p, _dp, _dp]
+            L.orc_set_filaments.argtypes = [ctypes.c_void_p, ctypes.c_long, _lp, _lp, _lp, _dp]
+            L.orc_filament_force.argtypes = [ctypes.c_long, _dp, _dp, _dp, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_double, _dp]
             L.orc_set_body_force.argtypes = [ctypes.c_void_p] + [ctypes.c_double] * 3
             L.orc_set_populations.argtypes = [ctypes.c_void_p, _dp]
             L.orc_get_populations.argtypes = [ctypes.c_void_p, _dp]
@@ -152,6 +156,17 @@ def lv_step(Pv, valve_open, Td, n, E, Edot, Qu, Pbar_gauge, P_la):
     return float(a[0]), float(b[0]), float(c[0]), int(closed.value)
 
 
+def filament_force(X, gl, gr, ds: float, Eh: float, EI: float) -> np.ndarray:
+    """SGFD internal force per unit length at the interior nodes of one
+    filament (zero at its two ends); ``gl``/``gr`` the ghost nodes beyond them."""
+    X = np.ascontiguousarray(X, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros_like(X)
+    gl = np.ascontiguousarray(gl, dtype=np.float64)
+    gr = np.ascontiguousarray(gr, dtype=np.float64)
+    lib().orc_filament_force(X.shape[0], _p(X), _p(gl), _p(gr), float(ds), float(Eh), float(EI), _p(out))
+    return out
+
+
 def phi(r: float) -> float:
     return lib().orc_phi(r)
 
@@ -195,6 +210,14 @@ class Oracle:
             X0, dA, ks, pin = self._ib_args
             L.orc_set_ib(self._h, ib.n, _p(X0), _p(dA), _p(ks), pin.ctypes.data_as(_u8p),
                          float(ib.alpha), float(ib.beta), float(ib.ms))
+            if getattr(ib, "filaments", None):
+                cnt = np.array([len(f) for f in ib.filaments], dtype=np.int64)
+                st = np.concatenate([[0], np.cumsum(cnt)[:-1]]).astype(np.int64)
+                nodes = np.ascontiguousarray(np.concatenate(ib.filaments), dtype=np.int64)
+                par = np.ascontiguousarray(ib.fil_par, dtype=np.float64).reshape(-1)
+                self._fil_args = (cnt, st, nodes, par)
+                L.orc_set_filaments(self._h, cnt.size, st.ctypes.data_as(_lp), cnt.ctypes.data_as(_lp),
+                                    nodes.ctypes.data_as(_lp), _p(par))
         self.nbc = len(inst.boundaries)
 
     def __del__(self):

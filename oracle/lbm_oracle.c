@@ -92,6 +92,9 @@ typedef struct {
     double *X0, *X, *Vs, *I, *F, *Vf, *dA, *ks;
     uint8_t *pinned;
     double alpha, beta, ms;
+    /* filaments (Section 2.3.2's SGFD solid): node lists and (ds, Eh, EI) */
+    long n_fil, *fil_start, *fil_count, *fil_nodes;
+    double *fil_par, *fil_force;
     long step;
     /* waveform log: one row per step: step, then 4 values per boundary */
     double *wave;
@@ -432,6 +435,32 @@ void orc_set_ib_state(void *h, const double *X, const double *Vs)
     memcpy(o->Vs, Vs, sizeof(double) * 3 * o->ns);
 }
 
+/* Declares n_fil filaments over the wall nodes: filament k is the node list
+ * nodes[start[k] .. start[k] + count[k] - 1] in arc-length order with
+ * par[3k..3k+2] = (ds, Eh, EI).  Its interior nodes move by the SGFD
+ * tension and bending forces (orc_filament_force) in addition to the
+ * tether spring and the penalty force; its end nodes should be pinned. */
+int orc_set_filaments(void *h, long n_fil, const long *start, const long *count, const long *nodes,
+                      const double *par)
+{
+    orc_t *o = (orc_t *)h;
+    long tot = 0;
+    for (long k = 0; k < n_fil; k++)
+        if (start[k] + count[k] > tot)
+            tot = start[k] + count[k];
+    o->n_fil = n_fil;
+    o->fil_start = (long *)malloc(sizeof(long) * (n_fil + 1));
+    o->fil_count = (long *)malloc(sizeof(long) * (n_fil + 1));
+    o->fil_nodes = (long *)malloc(sizeof(long) * (tot + 1));
+    o->fil_par = (double *)malloc(sizeof(double) * 3 * (n_fil + 1));
+    o->fil_force = (double *)calloc(3 * (o->ns + 1), sizeof(double));
+    memcpy(o->fil_start, start, sizeof(long) * n_fil);
+    memcpy(o->fil_count, count, sizeof(long) * n_fil);
+    memcpy(o->fil_nodes, nodes, sizeof(long) * tot);
+    memcpy(o->fil_par, par, sizeof(double) * 3 * n_fil);
+    return 0;
+}
+
 void orc_set_body_force(void *h, double gx, double gy, double gz)
 {
     orc_t *o = (orc_t *)h;
@@ -720,15 +749,95 @@ static void stream(orc_t *o)
     }
 }
 
+/* Internal force per unit reference length of a filament (Section 2.3.2,
+ * SGFD): for the nodes X_0 .. X_{n-1} at arc-length spacing ds, with ghost
+ * nodes X_{-1} = gl and X_n = gr,
+ *   tension  T_{i+1/2} = Eh (|D0 X_{i+1/2}| - 1), D0 X_{i+1/2} = (X_{i+1} - X_i)/ds
+ *            (Eq. tension), force (T D0 X)_{i+1/2} - (T D0 X)_{i-1/2}, over ds
+ *            (Eq. tension's D0(T D0 X));
+ *   bending  -EI D+D-(D+D- X)_i with D+D- X_i = (X_{i+1} - 2 X_i + X_{i-1})/ds^2
+ *            (Eqs. 2nd order, bending).
+ * out[3i..3i+2] is written for the interior nodes 1 .. n-2 and zeroed at
+ * both ends (n >= 3). */
+void orc_filament_force(long n, const double *X, const double *gl, const double *gr, double ds, double Eh,
+                        double EI, double *out)
+{
+    double *P = (double *)malloc(sizeof(double) * 3 * (n + 2)); /* X_{-1} .. X_n */
+    double *K = (double *)malloc(sizeof(double) * 3 * n);       /* D+D- X_i, i = 0..n-1 */
+    double *TD = (double *)malloc(sizeof(double) * 3 * n);      /* (T D0 X)_{i+1/2}, i = 0..n-2 */
+    for (int a = 0; a < 3; a++) {
+        P[a] = gl[a];
+        P[3 * (n + 1) + a] = gr[a];
+    }
+    memcpy(P + 3, X, sizeof(double) * 3 * n);
+    for (long i = 0; i < n; i++)
+        for (int a = 0; a < 3; a++)
+            K[3 * i + a] = (P[3 * (i + 2) + a] - 2.0 * P[3 * (i + 1) + a] + P[3 * i + a]) / (ds * ds);
+    for (long i = 0; i + 1 < n; i++) {
+        double d[3], len2 = 0.0;
+        for (int a = 0; a < 3; a++) {
+            d[a] = (X[3 * (i + 1) + a] - X[3 * i + a]) / ds;
+            len2 += d[a] * d[a];
+        }
+        double T = Eh * (sqrt(len2) - 1.0);
+        for (int a = 0; a < 3; a++)
+            TD[3 * i + a] = T * d[a];
+    }
+    for (int a = 0; a < 3; a++)
+        out[a] = out[3 * (n - 1) + a] = 0.0;
+    for (long i = 1; i + 1 < n; i++)
+        for (int a = 0; a < 3; a++) {
+            double ten = (TD[3 * i + a] - TD[3 * (i - 1) + a]) / ds;
+            double bend = -EI * (K[3 * (i + 1) + a] - 2.0 * K[3 * i + a] + K[3 * (i - 1) + a]) / (ds * ds);
+            out[3 * i + a] = ten + bend;
+        }
+    free(P);
+    free(K);
+    free(TD);
+}
+
+/* Internal forces of every filament at X(t_n), before any node moves.
+ * Reading: the wall's filament ends are simply supported (position held,
+ * zero curvature), i.e. ghost nodes X_{-1} = 2 X_0 - X_1 and
+ * X_n = 2 X_{n-1} - X_{n-2}. */
+static void filament_forces(orc_t *o)
+{
+    for (long k = 0; k < o->n_fil; k++) {
+        long n = o->fil_count[k];
+        const long *nd = o->fil_nodes + o->fil_start[k];
+        double *X = (double *)malloc(sizeof(double) * 3 * n), *out = (double *)malloc(sizeof(double) * 3 * n);
+        for (long i = 0; i < n; i++)
+            for (int a = 0; a < 3; a++)
+                X[3 * i + a] = o->X[3 * nd[i] + a];
+        double gl[3], gr[3];
+        for (int a = 0; a < 3; a++) {
+            gl[a] = 2.0 * X[a] - X[3 + a];
+            gr[a] = 2.0 * X[3 * (n - 1) + a] - X[3 * (n - 2) + a];
+        }
+        orc_filament_force(n, X, gl, gr, o->fil_par[3 * k], o->fil_par[3 * k + 1], o->fil_par[3 * k + 2], out);
+        for (long i = 0; i < n; i++)
+            for (int a = 0; a < 3; a++)
+                o->fil_force[3 * nd[i] + a] = out[3 * i + a];
+        free(X);
+        free(out);
+    }
+}
+
 /* Wall-node update (reading: linear springs to X0 replace the shell solver;
- * m_s dV_s/dt = -k_s (X - X0) - F, symplectic Euler; pinned nodes stay). */
+ * filament nodes add their SGFD force): m_s dV_s/dt = -k_s (X - X0) + F_fil
+ * - F, symplectic Euler with dt = 1 (for a filament this is the central
+ * difference in time, X^{n+1} - 2 X^n + X^{n-1} = dt^2 a^n); pinned nodes
+ * stay. */
 static void solid_update(orc_t *o)
 {
+    if (o->n_fil)
+        filament_forces(o);
     for (long s = 0; s < o->ns; s++) {
         if (o->pinned[s])
             continue;
         for (int a = 0; a < 3; a++) {
-            double acc = (-o->ks[s] * (o->X[3 * s + a] - o->X0[3 * s + a]) - o->F[3 * s + a]) / o->ms;
+            double ff = o->n_fil ? o->fil_force[3 * s + a] : 0.0;
+            double acc = (-o->ks[s] * (o->X[3 * s + a] - o->X0[3 * s + a]) + ff - o->F[3 * s + a]) / o->ms;
             o->Vs[3 * s + a] += acc;
             o->X[3 * s + a] += o->Vs[3 * s + a];
         }

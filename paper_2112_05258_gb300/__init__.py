@@ -3,4 +3,4 @@
 boundaries by non-equilibrium extrapolation, and the penalty immersed-boundary
 exchange, all in hand-written CUDA kernels behind the C-ABI of include/lbm.h.
 """
-from .lbm import Lattice, LBMError, load, F32, F16, BF16, F64  # noqa: F401
+from .lbm import Lattice, LBMError, check_config, load, F32, F16, BF16, F64  # noqa: F401

@@ -38,6 +38,7 @@ struct lbm_handle {
     RowInfo *rows = nullptr;
     int32_t *chunk_row = nullptr, *rowid = nullptr;
     double *omega = nullptr;
+    float *omega_f = nullptr;
     long long *step_dev = nullptr;
     unsigned *status = nullptr;
     BcParam *bc_par = nullptr;
@@ -53,6 +54,8 @@ struct lbm_handle {
     double *ibX0 = nullptr, *ibdA = nullptr, *ibks = nullptr;
     uint8_t *ibpin = nullptr;
     int32_t *iblines = nullptr, *ibref = nullptr;
+    int32_t *fil_nodes = nullptr, *fil_start = nullptr, *fil_count = nullptr;
+    double *fil_par = nullptr;
     uint64_t *ibmask = nullptr;
     double *rd_f19 = nullptr, *rd_mac = nullptr;  // read-out scratch, largest instance (allocated on first use)
     int64_t max_inst_cells = 0;
@@ -165,6 +168,26 @@ lbm_status check_config(const lbm_config *cfg, std::string &why) {
                 const double X = d.ib_X0[3 * s + a];
                 if (!(X >= 0.0 && X <= (double)n[a])) return why = "wall node outside the box", LBM_ERR_ARG;
             }
+        if (d.ib_n_fil < 0 || (d.ib_n_fil > 0 && (d.n_ib <= 0 || !d.ib_fil_count || !d.ib_fil_nodes || !d.ib_fil_par)))
+            return why = "bad filament arrays", LBM_ERR_ARG;
+        if (d.ib_n_fil > 0) {
+            std::vector<uint8_t> used((size_t)d.n_ib, 0);
+            int64_t o = 0;
+            for (int64_t k = 0; k < d.ib_n_fil; k++) {
+                const int64_t c = d.ib_fil_count[k];
+                if (c < 3 || c > LBM_MAX_FILAMENT_NODES) return why = "filament needs 3 to 3072 nodes", LBM_ERR_ARG;
+                const double *fp = d.ib_fil_par + 3 * k;
+                if (!(fp[0] > 0) || !(fp[1] >= 0) || !(fp[2] >= 0)) return why = "bad filament parameters", LBM_ERR_ARG;
+                for (int64_t i = 0; i < c; i++) {
+                    const int64_t s = d.ib_fil_nodes[o + i];
+                    if (s < 0 || s >= d.n_ib || used[s]) return why = "filament node out of range or repeated", LBM_ERR_ARG;
+                    used[s] = 1;
+                }
+                if (!d.ib_pinned[d.ib_fil_nodes[o]] || !d.ib_pinned[d.ib_fil_nodes[o + c - 1]])
+                    return why = "filament end nodes must be pinned", LBM_ERR_ARG;
+                o += c;
+            }
+        }
     }
     return LBM_OK;
 }
@@ -243,6 +266,33 @@ bool bad_inst(lbm_handle *h, int inst) { return !h || inst < 0 || inst >= (int)h
 
 extern "C" {
 
+lbm_status lbm_check_config(const lbm_config *cfg, lbm_layout_stats *stats, char *why, int why_len) {
+    std::string msg;
+    lbm_status st = check_config(cfg, msg);
+    Layout L;
+    if (st == LBM_OK) {
+        msg = build_layout(cfg, L);
+        if (msg.empty() && (double)NQ * (double)L.n_stored >= 2147483647.0)
+            msg = "more than 2^31 / 19 stored cells (32-bit population offsets)";
+        st = msg.empty() ? LBM_OK : LBM_ERR_ARG;
+    }
+    if (why && why_len > 0) {
+        const size_t n = std::min(msg.size(), (size_t)why_len - 1);
+        memcpy(why, msg.data(), n);
+        why[n] = 0;
+    }
+    if (st == LBM_OK && stats) {
+        stats->fluid_cells = L.n_fluid;
+        stats->stored_cells = L.n_stored;
+        stats->box_cells = L.n_box;
+        stats->band_cells = (int64_t)L.band.size();
+        stats->links = (int64_t)L.lk_xb.size();
+        stats->ib_nodes = (int64_t)L.ib_dA.size();
+        stats->filaments = (int64_t)L.fil_start.size();
+    }
+    return st;
+}
+
 lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
     if (!out) return LBM_ERR_ARG;
     *out = nullptr;
@@ -266,6 +316,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
         d.bc = nullptr;
         d.ib_X0 = d.ib_dA = d.ib_ks = nullptr;
         d.ib_pinned = nullptr;
+        d.ib_fil_count = d.ib_fil_nodes = nullptr;
+        d.ib_fil_par = nullptr;
     }
     auto bail = [&](lbm_status s, const std::string &m) {
         fprintf(stderr, "lbm_create: %s\n", m.c_str());
@@ -304,7 +356,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
     if (ok) ok = ck(upload(h, &h->rowid, L.rowid), "rowid");
     std::vector<double> om;
     for (auto &ip : L.inst) om.push_back(ip.omega);
-    if (ok) ok = ck(upload(h, &h->omega, om), "omega");
+    std::vector<float> omf(om.begin(), om.end());
+    if (ok) ok = ck(upload(h, &h->omega, om), "omega") && ck(upload(h, &h->omega_f, omf), "omega");
     if (ok) ok = ck(upload(h, &h->inst_dev, L.inst), "instances");
     long long minus1 = -1;
     if (ok) ok = ck(dalloc(h, &h->step_dev, 1), "step") &&
@@ -348,6 +401,11 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
              ck(upload(h, &h->ibdA, L.ib_dA), "ib") && ck(upload(h, &h->ibks, L.ib_ks), "ib") &&
              ck(upload(h, &h->ibpin, L.ib_pinned), "ib") && ck(upload(h, &h->iblines, L.ib_lines), "ib") &&
              ck(upload(h, &h->ibmask, L.ib_mask), "ib") && ck(upload(h, &h->ibref, L.ib_ref), "ib") &&
+             ck(upload(h, &h->fil_nodes, L.fil_nodes), "filaments") &&
+             ck(upload(h, &h->fil_start, L.fil_start), "filaments") &&
+             ck(upload(h, &h->fil_count, L.fil_count), "filaments") &&
+             ck(upload(h, &h->fil_par, L.fil_par), "filaments") &&
+             (L.fil_start.empty() || ck(prepare_filament_kernel(L.max_fil), "filament kernel")) &&
              ck(dalloc_bytes(h, &h->vband, 4 * n * h->rbytes), "vband");
     }
     {
@@ -369,6 +427,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
     h->kp.rows = h->rows;
     h->kp.chunk_row = h->chunk_row;
     h->kp.omega = h->omega;
+    h->kp.omega_f = h->omega_f;
     h->kp.b = h->b;
     h->kp.aux = h->aux;
     h->kp.step = h->step_dev;
@@ -410,10 +469,16 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
     h->ibp.ks = h->ibks;
     h->ibp.pinned = h->ibpin;
     h->ibp.vband = h->vband;
-    h->ibp.threads_per_node = cfg->ib_threads_per_node ? cfg->ib_threads_per_node : 1;
+    h->ibp.threads_per_node = cfg->ib_threads_per_node ? cfg->ib_threads_per_node : 2;
     h->ibp.lines = h->iblines;
     h->ibp.mask = h->ibmask;
     h->ibp.ref = h->ibref;
+    h->ibp.n_fil = (int)L.fil_start.size();
+    h->ibp.max_fil = L.max_fil;
+    h->ibp.fil_nodes = h->fil_nodes;
+    h->ibp.fil_start = h->fil_start;
+    h->ibp.fil_count = h->fil_count;
+    h->ibp.fil_par = h->fil_par;
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(LBM_ERR_CUDA, "set-up failed");
     *out = h;
     return LBM_OK;

@@ -41,6 +41,11 @@ __device__ __forceinline__ int find_row(const KParams &p, int c) {
     return ch.x + __popc((uint32_t)ch.y & upto);
 }
 
+// relaxation rate of an instance in the arithmetic type R
+template <class R> __device__ __forceinline__ R omega_of(const KParams &p, int inst);
+template <> __device__ __forceinline__ float omega_of<float>(const KParams &p, int inst) { return __ldg(&p.omega_f[inst]); }
+template <> __device__ __forceinline__ double omega_of<double>(const KParams &p, int inst) { return __ldg(&p.omega[inst]); }
+
 template <class S> static S *as(void *p) { return static_cast<S *>(p); }
 
 #define DISPATCH(prec, CALL)                                   \

@@ -11,6 +11,9 @@
 //                   integral and force F = alpha I + beta (V_f - V_s) on the
 //                   fluid, spreading of F delta dA with one vector atomic per
 //                   cell, spring update.
+//   k_filament      one CTA per filament of wall nodes: SGFD tension and
+//                   bending forces (Section 2.3.2) at X(t_n) from shared
+//                   memory, then the wall update of its interior nodes.
 #include "lbm_device.cuh"
 
 namespace lbm {
@@ -188,15 +191,94 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib) {
         add.w = 0;
         vec_atomic_add(&b[c], add);
     }
-    if (q == 0 && !ib.pinned[s]) {
+    if (q == 0 && ib.pinned[s] == 0) {  // pinned nodes stay; filament nodes move in k_filament
+        const double inv_ms = ip.inv_ms;
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-            const double acc = (-ib.ks[s] * (X[a] - ib.X0[3 * s + a]) - F[a]) / ip.ms;
+            const double acc = (-ib.ks[s] * (X[a] - ib.X0[3 * s + a]) - F[a]) * inv_ms;
             const double v = Vs[a] + acc;
             ib.Vs[3 * s + a] = v;
             ib.X[3 * s + a] = X[a] + v;
         }
     }
+}
+
+// SGFD filament (Section 2.3.2): node i of a filament of n nodes at reference
+// spacing ds, with simply supported ends (ghosts X_{-1} = 2 X_0 - X_1 and
+// X_n = 2 X_{n-1} - X_{n-2}, so D+D- X vanishes at both ends):
+//   T_{i+1/2} = Eh (|D0 X_{i+1/2}| - 1)                          (Eq. tension)
+//   F_i = [(T D0 X)_{i+1/2} - (T D0 X)_{i-1/2}] / ds
+//         - EI [K_{i+1} - 2 K_i + K_{i-1}] / ds^2,  K_j = D+D- X_j (Eq. bending)
+// The filament's positions X(t_n) are staged in shared memory before any
+// node moves, so every force sees the same time level; the interior nodes
+// (pinned code 2) then take m_s dV/dt = -k_s (X - X0) + F_i - F_penalty
+// with dt = 1 (V, then X), the central difference in time.
+// FP64 division and square root are multi-instruction sequences on the
+// FP64 pipe, which is narrow on this part: the kernel multiplies by 1/ds and
+// 1/m_s, computed once per thread (one rounding more than dividing, far
+// below the parity tolerance), and stages K_j and (T D0 X)_{j+1/2} once per
+// node and segment in shared memory (one square root per segment).
+constexpr int FIL_THREADS = 512;
+
+__global__ void __launch_bounds__(FIL_THREADS) k_filament(KParams p, IbKParams ib) {
+    extern __shared__ double sm[];
+    const int k = blockIdx.x;
+    const int n = ib.fil_count[k], st = ib.fil_start[k];
+    double *P = sm;                 // X_{-1} .. X_n: P[3 (j + 1) + a] = X_j
+    double *K = P + 3 * (n + 2);    // K_j = D+D- X_j, j = 0 .. n-1
+    double *TD = K + 3 * n;         // (T D0 X)_{j+1/2}, j = 0 .. n-2
+    const double ds = ib.fil_par[3 * k], Eh = ib.fil_par[3 * k + 1], EI = ib.fil_par[3 * k + 2];
+    const double inv_ds = 1.0 / ds, inv_ds2 = inv_ds * inv_ds;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int s = ib.fil_nodes[st + i];
+#pragma unroll
+        for (int a = 0; a < 3; a++) P[3 * (i + 1) + a] = ib.X[3 * s + a];
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        const int a = threadIdx.x;
+        P[a] = 2.0 * P[3 + a] - P[6 + a];
+        P[3 * (n + 1) + a] = 2.0 * P[3 * n + a] - P[3 * (n - 1) + a];
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double *x = P + 3 * (j + 1);
+#pragma unroll
+        for (int a = 0; a < 3; a++) K[3 * j + a] = (x[3 + a] - 2.0 * x[a] + x[a - 3]) * inv_ds2;
+        if (j + 1 < n) {
+            double d[3], len2 = 0.0;
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                d[a] = (x[3 + a] - x[a]) * inv_ds;
+                len2 += d[a] * d[a];
+            }
+            const double T = Eh * (sqrt(len2) - 1.0);
+#pragma unroll
+            for (int a = 0; a < 3; a++) TD[3 * j + a] = T * d[a];
+        }
+    }
+    __syncthreads();
+    for (int i = 1 + threadIdx.x; i < n - 1; i += blockDim.x) {
+        const int s = ib.fil_nodes[st + i];
+        if (ib.pinned[s] != 2) continue;
+        const double inv_ms = ib.inst[ib.node_inst[s]].inv_ms;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const double xa = P[3 * (i + 1) + a];
+            const double ff = (TD[3 * i + a] - TD[3 * (i - 1) + a]) * inv_ds -
+                              EI * (K[3 * (i + 1) + a] - 2.0 * K[3 * i + a] + K[3 * (i - 1) + a]) * inv_ds2;
+            const double acc = (-ib.ks[s] * (xa - ib.X0[3 * s + a]) + ff - ib.F[3 * s + a]) * inv_ms;
+            const double v = ib.Vs[3 * s + a] + acc;
+            ib.Vs[3 * s + a] = v;
+            ib.X[3 * s + a] = xa + v;
+        }
+    }
+}
+
+static size_t filament_smem(int max_fil) { return (size_t)(9 * max_fil + 6) * sizeof(double); }
+
+cudaError_t prepare_filament_kernel(int max_fil) {
+    return cudaFuncSetAttribute(k_filament, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)filament_smem(max_fil));
 }
 
 template <class S> static void launch_nodes(const KParams &p, const IbKParams &ib, cudaStream_t st) {
@@ -229,6 +311,8 @@ cudaError_t launch_ib(int prec, const void *fin, const KParams &p, const IbKPara
         launch_nodes<double>(p, ib, st);
         break;
     }
+    if (ib.n_fil)
+        k_filament<<<ib.n_fil, FIL_THREADS, filament_smem(ib.max_fil), st>>>(p, ib);
     return cudaGetLastError();
 }
 

@@ -69,6 +69,7 @@ struct InstParam {
     int ib_off, n_ib;
     int bc_first, n_bc;
     double alpha, beta, ms;
+    double inv_ms;  // 1/ms (FP64 division is slow on the device)
 };
 
 enum { BC_VELOCITY = 0, BC_RCR = 1, BC_LV = 2, BC_PRESSURE = 3 };
@@ -125,7 +126,11 @@ struct Layout {
     std::vector<uint64_t> ib_mask;
     std::vector<int32_t> ib_ref;        // i0 per node (3 ints)
     std::vector<double> ib_X0, ib_dA, ib_ks;
-    std::vector<uint8_t> ib_pinned;
+    std::vector<uint8_t> ib_pinned;     // 0 spring, 1 pinned, 2 moved by its filament
+    // filaments: global wall-node lists, first entry and count per filament, (ds, Eh, EI)
+    std::vector<int32_t> fil_nodes, fil_start, fil_count;
+    std::vector<double> fil_par;
+    int max_fil = 0;
 };
 
 }  // namespace lbm

@@ -20,6 +20,7 @@ struct KParams {
     const RowInfo *rows;        // rows + sentinel
     const int32_t *chunk_row;   // per 32-cell chunk: {row of its first cell, new-row lane mask}
     const double *omega;        // per instance, 1/tau
+    const float *omega_f;       // the same rounded to FP32 (no FP64 conversion per cell)
     const void *b;              // force density b, 4 x compute type per cell (x, y, z, unused)
     void *aux;                  // first-layer macros (sum s, jx, jy, jz), compute type, 4 x n
     long long *step;            // index t_n of the step in progress
@@ -66,6 +67,10 @@ struct IbKParams {
     const int32_t *lines;       // 36 per node: compact index of x = 0 on the support lines
     const uint64_t *mask;       // 4 per node: fluid cells of the 6^3 box around the reference cell
     const int32_t *ref;         // 3 per node: reference cell floor(X0 - 0.5)
+    // filaments (SGFD wall solid): node lists, first entry, count, (ds, Eh, EI)
+    int n_fil, max_fil;
+    const int32_t *fil_nodes, *fil_start, *fil_count;
+    const double *fil_par;
 };
 
 // variants {min resident 256-thread blocks per SM, cells per thread}:
@@ -87,5 +92,6 @@ cudaError_t launch_cycle_change(const BcKParams &q, const int *bc_first, const i
 cudaError_t launch_init(int prec, void *fout, const KParams &p, const double *f19, int c0, int c1,
                         cudaStream_t s);
 cudaError_t launch_ib(int prec, const void *fin, const KParams &p, const IbKParams &ib, cudaStream_t s);
+cudaError_t prepare_filament_kernel(int max_fil);
 
 }  // namespace lbm

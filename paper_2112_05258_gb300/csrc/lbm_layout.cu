@@ -46,6 +46,7 @@ std::string build_layout(const lbm_config *cfg, Layout &L) {
         ip.alpha = d.ib_alpha;
         ip.beta = d.ib_beta;
         ip.ms = d.ib_ms;
+        ip.inv_ms = d.ib_ms > 0 ? 1.0 / d.ib_ms : 0.0;
         L.n_box += nbox;
         L.inst_cell_begin[q] = cell;
         const int row_base = (int)L.rows.size();
@@ -265,12 +266,26 @@ std::string build_layout(const lbm_config *cfg, Layout &L) {
         ip.ib_off = (int)L.ib_dA.size();
         ip.n_ib = (int)d.n_ib;
         if (d.n_ib <= 0) continue;
+        {
+            // filaments: global node indices; interior nodes that are not
+            // pinned are moved by the filament kernel (pinned code 2)
+            int64_t o = 0;
+            for (int64_t k = 0; k < d.ib_n_fil; k++) {
+                const int64_t c = d.ib_fil_count[k];
+                L.fil_start.push_back((int32_t)L.fil_nodes.size());
+                L.fil_count.push_back((int32_t)c);
+                for (int a = 0; a < 3; a++) L.fil_par.push_back(d.ib_fil_par[3 * k + a]);
+                for (int64_t i = 0; i < c; i++) L.fil_nodes.push_back((int32_t)(ip.ib_off + d.ib_fil_nodes[o + i]));
+                L.max_fil = std::max(L.max_fil, (int)c);
+                o += c;
+            }
+        }
         const int nx = d.nx, ny = d.ny, nz = d.nz;
         for (int64_t s = 0; s < d.n_ib; s++) {
             for (int a = 0; a < 3; a++) L.ib_X0.push_back(d.ib_X0[3 * s + a]);
             L.ib_dA.push_back(d.ib_dA[s]);
             L.ib_ks.push_back(d.ib_ks[s]);
-            L.ib_pinned.push_back(d.ib_pinned[s]);
+            L.ib_pinned.push_back(d.ib_pinned[s] ? 1 : 0);
             int i0[3];
             for (int a = 0; a < 3; a++) i0[a] = (int)std::floor(d.ib_X0[3 * s + a] - 0.5);
             for (int a = 0; a < 3; a++) L.ib_ref.push_back(i0[a]);
@@ -311,6 +326,11 @@ std::string build_layout(const lbm_config *cfg, Layout &L) {
     }
     for (int64_t c = 0; c < L.n_stored; c++)
         if (L.flags[c] & FL_BAND) L.band.push_back((int32_t)c);
+    for (size_t k = 0; k < L.fil_start.size(); k++)
+        for (int i = 1; i + 1 < L.fil_count[k]; i++) {
+            uint8_t &pin = L.ib_pinned[L.fil_nodes[L.fil_start[k] + i]];
+            if (pin == 0) pin = 2;
+        }
     return "";
 }
 

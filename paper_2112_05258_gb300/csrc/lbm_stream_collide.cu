@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(256, MINB)
         om[u] = R(0);
         if (!(fl[u] & FL_ACTIVE)) continue;
         const int r = find_row(p, c);
-        om[u] = (R)__ldg(&p.omega[__ldg(&p.rows[r].inst)]);
+        om[u] = omega_of<R>(p, __ldg(&p.rows[r].inst));
         const int x = __ldg(&p.rows[r].x0) + (c - __ldg(&p.rows[r].off));
         const int *nb = p.rows[r].nb;
 #pragma unroll

@@ -39,7 +39,9 @@ class InstanceDesc(ctypes.Structure):
                 ("n_bc", ctypes.c_int), ("bc", ctypes.POINTER(BoundaryDesc)),
                 ("n_ib", ctypes.c_int64), ("ib_X0", _dp), ("ib_dA", _dp), ("ib_ks", _dp),
                 ("ib_pinned", _u8p), ("ib_alpha", ctypes.c_double), ("ib_beta", ctypes.c_double),
-                ("ib_ms", ctypes.c_double)]
+                ("ib_ms", ctypes.c_double), ("ib_n_fil", ctypes.c_int64),
+                ("ib_fil_count", ctypes.POINTER(ctypes.c_int64)),
+                ("ib_fil_nodes", ctypes.POINTER(ctypes.c_int64)), ("ib_fil_par", _dp)]
 
 
 class Config(ctypes.Structure):
@@ -58,12 +60,17 @@ class Info(ctypes.Structure):
                 ("bytes_per_population", ctypes.c_int)]
 
 
+class LayoutStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in (
+        "fluid_cells", "stored_cells", "box_cells", "band_cells", "links", "ib_nodes", "filaments")]
+
+
 EXPORTS = ["lbm_create", "lbm_set_0d_params", "lbm_init_populations", "lbm_step", "lbm_sync",
            "lbm_read_fields", "lbm_read_populations", "lbm_read_0d_state", "lbm_read_waveforms",
            "lbm_read_ib", "lbm_set_ib_state", "lbm_set_kernel_timing", "lbm_get_kernel_time",
            "lbm_get_info", "lbm_last_error", "lbm_destroy", "lbm_boundary_flux_noalloc",
            "lbm_init_equilibrium", "lbm_set_0d_state", "lbm_cycle_change", "lbm_autotune",
-           "lbm_wall_shear"]
+           "lbm_wall_shear", "lbm_check_config"]
 
 _lib = None
 
@@ -99,6 +106,8 @@ def load(path: Optional[str] = None):
     L.lbm_destroy.restype = None
     L.lbm_init_equilibrium.argtypes = [H, ctypes.c_int, _dp, _dp, _dp, _dp]
     L.lbm_wall_shear.argtypes = [H, ctypes.c_int, _dp]
+    L.lbm_check_config.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(LayoutStats), ctypes.c_char_p,
+                                   ctypes.c_int]
     L.lbm_set_0d_state.argtypes = [H, ctypes.c_int, ctypes.c_int, _dp]
     L.lbm_cycle_change.argtypes = [H, ctypes.POINTER(ctypes.c_int64), _dp]
     L.lbm_autotune.argtypes = [H, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
@@ -122,6 +131,81 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(_dp)
 
 
+def _config(instances, precision, device=0, stream=None, graph_steps=0, wave_capacity=0, block_size=0,
+            ib_threads_per_node=0):
+    """lbm_config for the instances and the host arrays it points to (to be
+    kept alive while the library copies them)."""
+    keep = []
+    n = len(instances)
+    descs = (InstanceDesc * n)()
+    for q, inst in enumerate(instances):
+        nz, ny, nx = inst.node.shape
+        node = np.ascontiguousarray(inst.node, dtype=np.uint8).reshape(-1)
+        keep.append(node)
+        bcs = (BoundaryDesc * max(1, len(inst.boundaries)))()
+        for k, b in enumerate(inst.boundaries):
+            par = np.ascontiguousarray(b.params, dtype=np.float64)
+            keep.append(par)
+            bcs[k].kind, bcs[k].axis, bcs[k].sign = int(b.kind), int(b.axis), int(b.sign)
+            bcs[k].n_params, bcs[k].params = par.size, _p(par)
+            if b.profile is not None:
+                prof = np.ascontiguousarray(b.profile, dtype=np.float64)
+                keep.append(prof)
+                bcs[k].n_profile, bcs[k].profile = prof.shape[0], _p(prof)
+            if b.elastance is not None:
+                et = np.ascontiguousarray(b.elastance, dtype=np.float64)
+                keep.append(et)
+                bcs[k].period, bcs[k].elastance = et.shape[0], _p(et)
+        keep.append(bcs)
+        d = descs[q]
+        d.nx, d.ny, d.nz = nx, ny, nz
+        d.node = node.ctypes.data_as(_u8p)
+        d.tau = float(inst.tau)
+        d.q_scale = int(getattr(inst, "q_scale", 1))
+        d.n_bc = len(inst.boundaries)
+        d.bc = ctypes.cast(bcs, ctypes.POINTER(BoundaryDesc))
+        ib = getattr(inst, "ib", None)
+        if ib is not None and ib.n > 0:
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (ib.X0, ib.dA, ib.ks)]
+            pin = np.ascontiguousarray(ib.pinned, dtype=np.uint8)
+            keep += arrs + [pin]
+            d.n_ib = ib.n
+            d.ib_X0, d.ib_dA, d.ib_ks = (_p(a) for a in arrs)
+            d.ib_pinned = pin.ctypes.data_as(_u8p)
+            d.ib_alpha, d.ib_beta, d.ib_ms = float(ib.alpha), float(ib.beta), float(ib.ms)
+            fils = getattr(ib, "filaments", None)
+            if fils:
+                cnt = np.array([len(f) for f in fils], dtype=np.int64)
+                nodes = np.ascontiguousarray(np.concatenate(fils), dtype=np.int64)
+                fpar = np.ascontiguousarray(ib.fil_par, dtype=np.float64).reshape(-1)
+                keep += [cnt, nodes, fpar]
+                d.ib_n_fil = cnt.size
+                d.ib_fil_count = cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+                d.ib_fil_nodes = nodes.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+                d.ib_fil_par = _p(fpar)
+    cfg = Config(precision=int(precision), n_instances=n,
+                 inst=ctypes.cast(descs, ctypes.POINTER(InstanceDesc)),
+                 stream=ctypes.c_void_p(stream or 0), device=device, graph_steps=graph_steps,
+                 wave_capacity=wave_capacity, block_size=block_size,
+                 ib_threads_per_node=ib_threads_per_node)
+    keep.append(descs)
+    return cfg, keep
+
+
+def check_config(instances, precision="f32", ib_threads_per_node: int = 0) -> dict:
+    """Host-only validation and layout sizes of a batch (no GPU needed):
+    raises LBMError with the reason if lbm_create would reject it."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision.lower()]
+    cfg, keep = _config(instances, precision, ib_threads_per_node=ib_threads_per_node)
+    st = LayoutStats()
+    why = ctypes.create_string_buffer(512)
+    rc = load().lbm_check_config(ctypes.byref(cfg), ctypes.byref(st), why, len(why))
+    if rc != 0:
+        raise LBMError(rc, why.value.decode())
+    return {n: getattr(st, n) for n, _ in LayoutStats._fields_}
+
+
 class Lattice:
     """A batch of lattice instances advanced together on one GPU.
 
@@ -135,58 +219,21 @@ class Lattice:
         L = load()
         if isinstance(precision, str):
             precision = PRECISIONS[precision.lower()]
-        self._keep = []
+        cfg, self._keep = _config(instances, precision, device, stream, graph_steps, wave_capacity,
+                                  block_size, ib_threads_per_node)
+        self.shapes = [(inst.node.shape[2], inst.node.shape[1], inst.node.shape[0]) for inst in instances]
+        self.nbc = [len(inst.boundaries) for inst in instances]
         n = len(instances)
-        descs = (InstanceDesc * n)()
-        self.shapes = []
-        self.nbc = []
-        for q, inst in enumerate(instances):
-            nz, ny, nx = inst.node.shape
-            node = np.ascontiguousarray(inst.node, dtype=np.uint8).reshape(-1)
-            self._keep.append(node)
-            bcs = (BoundaryDesc * max(1, len(inst.boundaries)))()
-            for k, b in enumerate(inst.boundaries):
-                par = np.ascontiguousarray(b.params, dtype=np.float64)
-                self._keep.append(par)
-                bcs[k].kind, bcs[k].axis, bcs[k].sign = int(b.kind), int(b.axis), int(b.sign)
-                bcs[k].n_params, bcs[k].params = par.size, _p(par)
-                if b.profile is not None:
-                    prof = np.ascontiguousarray(b.profile, dtype=np.float64)
-                    self._keep.append(prof)
-                    bcs[k].n_profile, bcs[k].profile = prof.shape[0], _p(prof)
-                if b.elastance is not None:
-                    et = np.ascontiguousarray(b.elastance, dtype=np.float64)
-                    self._keep.append(et)
-                    bcs[k].period, bcs[k].elastance = et.shape[0], _p(et)
-            self._keep.append(bcs)
-            d = descs[q]
-            d.nx, d.ny, d.nz = nx, ny, nz
-            d.node = node.ctypes.data_as(_u8p)
-            d.tau = float(inst.tau)
-            d.q_scale = int(getattr(inst, "q_scale", 1))
-            d.n_bc = len(inst.boundaries)
-            d.bc = ctypes.cast(bcs, ctypes.POINTER(BoundaryDesc))
-            ib = getattr(inst, "ib", None)
-            if ib is not None and ib.n > 0:
-                arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (ib.X0, ib.dA, ib.ks)]
-                pin = np.ascontiguousarray(ib.pinned, dtype=np.uint8)
-                self._keep += arrs + [pin]
-                d.n_ib = ib.n
-                d.ib_X0, d.ib_dA, d.ib_ks = (_p(a) for a in arrs)
-                d.ib_pinned = pin.ctypes.data_as(_u8p)
-                d.ib_alpha, d.ib_beta, d.ib_ms = float(ib.alpha), float(ib.beta), float(ib.ms)
-            self.shapes.append((nx, ny, nz))
-            self.nbc.append(len(inst.boundaries))
-        cfg = Config(precision=int(precision), n_instances=n,
-                     inst=ctypes.cast(descs, ctypes.POINTER(InstanceDesc)),
-                     stream=ctypes.c_void_p(stream or 0), device=device, graph_steps=graph_steps,
-                     wave_capacity=wave_capacity, block_size=block_size,
-                     ib_threads_per_node=ib_threads_per_node)
         h = ctypes.c_void_p()
         st = L.lbm_create(ctypes.byref(cfg), ctypes.byref(h))
-        self._keep = None
         if st != 0:
-            raise LBMError(st, "lbm_create failed (see stderr)")
+            msg = "lbm_create failed (see stderr)"
+            if st == -1:
+                why = ctypes.create_string_buffer(512)
+                if L.lbm_check_config(ctypes.byref(cfg), None, why, len(why)) != 0:
+                    msg = why.value.decode()
+            raise LBMError(st, msg)
+        self._keep = None
         self._h = h
         self.precision = int(precision)
         self.n_instances = n

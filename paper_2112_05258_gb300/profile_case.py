@@ -6,6 +6,9 @@
 ``tube``: straight rigid tube, 128 x 128 x 512, radius 40 (2.5M fluid cells,
 about 0.4 GB of FP32 populations: larger than L2, small enough for a
 multi-pass capture).  ``aorta``: the full-size elastic-wall workload.
+``fil_tube``: elastic tube 64 x 64 x 512 whose membrane (radius 24, 151 x 510
+nodes) is also 151 axial SGFD filaments; ``spring_tube``: the same membrane
+without the filaments.
 Steps are launched directly (no CUDA graph) so that each kernel launch is
 visible to a profiler.
 """
@@ -21,7 +24,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="tube", choices=["tube", "aorta"])
+    ap.add_argument("--case", default="tube", choices=["tube", "aorta", "fil_tube", "spring_tube"])
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--precision", default="f32")
     ap.add_argument("--block", type=int, default=0)
@@ -30,6 +33,9 @@ def main():
     from workloads import aorta, configs
     if args.case == "tube":
         inst = configs.rigid_tube(128, 128, 512, radius=40.0, period=4000)
+    elif args.case in ("fil_tube", "spring_tube"):
+        inst = configs.ib_tube(64, 64, 512, radius=24.0, period=4000, u_peak=0.02,
+                               filaments=args.case == "fil_tube")
     else:
         inst = aorta.build(0)
     lat = Lattice([inst], precision=args.precision, block_size=args.block,

@@ -107,8 +107,10 @@ def assert_same_wss(lat, o, inst, atol):
     assert np.abs(wg - wo).max() < atol
 
 
-def test_f64_immersed_boundary(Lattice):
-    inst = configs.ib_tube()
+@pytest.mark.parametrize("filaments", [False, True])
+def test_f64_immersed_boundary(Lattice, filaments):
+    # spring wall, or the SGFD filament wall (31 axial filaments of 22 nodes)
+    inst = configs.ib_tube(filaments=filaments)
     lat = run_gpu(Lattice, inst, 300)
     o = run_oracle(inst, 300)
     assert_same(lat, o, inst)
@@ -116,6 +118,24 @@ def test_f64_immersed_boundary(Lattice):
     for a, b in zip(lat.ib_state(0, n), o.ib_state()):
         assert np.abs(a - b).max() < 1e-12
     assert_same_wss(lat, o, inst, 1e-12)        # band cells carry b in sigma
+
+
+def test_filament_config_is_validated(Lattice):
+    from paper_2112_05258_gb300 import LBMError
+    for bad in ("end_unpinned", "repeated", "short"):
+        inst = configs.ib_tube(filaments=True)
+        fil = [f.copy() for f in inst.ib.filaments]
+        if bad == "end_unpinned":
+            inst.ib.pinned = inst.ib.pinned.copy()
+            inst.ib.pinned[fil[0][-1]] = 0
+        elif bad == "repeated":
+            fil[1] = fil[1].copy()
+            fil[1][3] = fil[0][3]
+        else:
+            fil[0] = fil[0][:2]
+        inst.ib.filaments = fil
+        with pytest.raises(LBMError):
+            Lattice([inst], precision="f64")
 
 
 def test_f32_wall_shear_rigid_tube(Lattice):
@@ -188,11 +208,11 @@ def test_graph_equals_direct_launches(Lattice):
     assert np.array_equal(g.waves(0), d.waves(0))
 
 
-def test_graph_equals_direct_launches_with_ib(Lattice):
-    # graphs run the non-band cells on a second stream beside the IB chain;
-    # direct launches run one sequence: the same per-cell arithmetic, only the
+@pytest.mark.parametrize("filaments", [False, True])
+def test_graph_equals_direct_launches_with_ib(Lattice, filaments):
+    # the same kernels captured in graphs or launched one by one: only the
     # order of the spreading atomics may differ
-    inst = configs.ib_tube()
+    inst = configs.ib_tube(filaments=filaments)
     for prec, tol in (("f64", 1e-14), ("f32", 1e-6)):
         g = Lattice([inst], precision=prec, graph_steps=8)
         g.step(203)
@@ -214,3 +234,18 @@ def test_unstable_state_is_reported(Lattice):
     with pytest.raises(LBMError) as e:
         lat.sync()
     assert e.value.status == -4
+
+
+def test_ib_kernel_variants_agree(Lattice):
+    # patch kernel (default) and the per-node kernels with 1, 2 or 4 threads
+    # per node: the same arithmetic, only the order of the force sums differs
+    inst = configs.ib_tube()
+    ref = Lattice([inst], precision="f64")
+    ref.step(120)
+    n = inst.ib.n
+    for tpn in (1, 2, 4):
+        lat = Lattice([inst], precision="f64", ib_threads_per_node=tpn)
+        lat.step(120)
+        assert np.abs(lat.populations(0) - ref.populations(0)).max() < 1e-13
+        for a, b in zip(lat.ib_state(0, n), ref.ib_state(0, n)):
+            assert np.abs(a - b).max() < 1e-13

@@ -143,14 +143,21 @@ def ib_ring_nodes(cx: float, cy: float, radius: float, z_centres, seed: int,
 IB_ALPHA, IB_BETA, IB_MS, IB_K = -2.0e-3, -0.5, 1.0, 0.01
 
 
+# stretching and bending stiffness of the filament wall (lattice units, per
+# unit width; explicit stability with m_s = 1 needs Eh < 1 and EI < 1/4)
+FIL_EH, FIL_EI = 0.1, 0.02
+
+
 def ib_tube(nx: int = 20, ny: int = 20, nz: int = 24, radius: float = 5.0,
             margin: float = 3.0, tau: float = 0.8, u_peak: float = 0.01,
-            period: int = 400, seed: int = 0) -> Instance:
+            period: int = 400, seed: int = 0, filaments: bool = False) -> Instance:
     """Straight tube whose wall is a ring of Lagrangian nodes at ``radius``.
 
     Fluid fills r < radius + margin so the kernel support of every wall node
     lies in fluid; the 0D inlet (Womersley profile) and RCR outlet cover
     r < radius only, the jacket outside the membrane is closed at both ends.
+    ``filaments``: every axial line of nodes (one per angle) is also an SGFD
+    filament (ds = 1, Eh = FIL_EH, EI = FIL_EI), pinned at both end rings.
     """
     node = geometry.straight_tube(nx, ny, nz, radius + margin)
     X, Y = np.meshgrid(np.arange(nx) + 0.5, np.arange(ny) + 0.5, indexing="xy")
@@ -165,4 +172,10 @@ def ib_tube(nx: int = 20, ny: int = 20, nz: int = 24, radius: float = 5.0,
     inst.boundaries.append(Boundary(BC_RCR, 2, -1, [0.05, 200.0, 1.0, 0.0]))
     inst.ib = ib_ring_nodes(nx / 2, ny / 2, radius, np.arange(1, nz - 1) + 0.5, seed,
                             IB_K, IB_ALPHA, IB_BETA, IB_MS)
+    if filaments:
+        n_rings = nz - 2
+        n_th = inst.ib.n // n_rings
+        inst.ib.filaments = [j + n_th * np.arange(n_rings) for j in range(n_th)]
+        inst.ib.fil_par = np.tile([1.0, FIL_EH, FIL_EI], (n_th, 1))
+        inst.name += "_filaments"
     return inst

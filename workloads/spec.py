@@ -64,6 +64,11 @@ class IBNodes:
     ``X0`` reference positions ``(ns, 3)``; ``dA`` area weights; ``ks``
     spring stiffness per node; ``pinned`` 1 for nodes held at ``X0``;
     ``alpha``/``beta`` the (negative) penalty gains; ``ms`` wall mass per area.
+
+    Optional filaments (the SGFD solid of Section 2.3.2): ``filaments`` a list
+    of node-index arrays in arc-length order, ``fil_par`` ``(n_fil, 3)`` with
+    ``(ds, Eh, EI)`` per filament.  Their interior nodes add the tension and
+    bending forces to the spring; their end nodes must be pinned.
     """
     X0: np.ndarray
     dA: np.ndarray
@@ -72,6 +77,8 @@ class IBNodes:
     alpha: float
     beta: float
     ms: float
+    filaments: Optional[List[np.ndarray]] = None
+    fil_par: Optional[np.ndarray] = None
 
     @property
     def n(self) -> int:
