@@ -58,6 +58,8 @@ def lib():
             L.orc_set_ib.argtypes = [ctypes.c_void_p, ctypes.c_long, _dp, _dp, _dp, _u8p,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_double]
             L.orc_set_ib_state.argtypes = [ctypes.c_void_p, _dp, _dp]
+            L.orc_lv_step_ord.argtypes = [_dp, _dp, _dp, ctypes.c_long] + [ctypes.c_double] * 4 + \
+                [ctypes.c_int] + [ctypes.c_double] * 3 + [ctypes.POINTER(ctypes.c_int)]
             L.orc_set_filaments.argtypes = [ctypes.c_void_p, ctypes.c_long, _lp, _lp, _lp, _dp]
             L.orc_filament_force.argtypes = [ctypes.c_long, _dp, _dp, _dp, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_double, _dp]
@@ -153,6 +155,16 @@ def lv_step(Pv, valve_open, Td, n, E, Edot, Qu, Pbar_gauge, P_la):
     closed = ctypes.c_int(0)
     lib().orc_lv_step(_p(a), _p(b), _p(c), n, E, Edot, Qu, Pbar_gauge, P_la,
                       ctypes.byref(closed))
+    return float(a[0]), float(b[0]), float(c[0]), int(closed.value)
+
+
+def lv_step_ord(Pv, valve_open, Td, n, E, Edot, E1, Edot1, order, Qu, Pbar_gauge, P_la):
+    """lv_step marched at the given order with the elastance table values at
+    t_n (E, Edot) and t_{n+1} (E1, Edot1)."""
+    a = np.array([Pv]); b = np.array([valve_open]); c = np.array([Td])
+    closed = ctypes.c_int(0)
+    lib().orc_lv_step_ord(_p(a), _p(b), _p(c), n, E, Edot, E1, Edot1, int(order), Qu, Pbar_gauge, P_la,
+                          ctypes.byref(closed))
     return float(a[0]), float(b[0]), float(c[0]), int(closed.value)
 
 

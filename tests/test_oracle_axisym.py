@@ -1,0 +1,109 @@
+"""Pins of the axisymmetric D2Q9 oracle (Section 2.3.1, Eq. Afi with the
+axisymmetric source; readings in oracle/axisym.py) against closed forms of
+axisymmetric pipe flow.
+
+* a fluid at rest stays at rest exactly;
+* steady Hagen-Poiseuille flow u = G (R^2 - r^2) / (4 nu) in a periodic pipe,
+  second order in R (the planar lattice alone would give twice that);
+* Womersley flow (J0 profile) under an oscillating axial force, second order
+  under diffusive scaling;
+* mass: through a stenosis between a velocity inlet and a pressure outlet
+  the flow rate 2 pi sum r u_x is the same at every cross-section to the
+  staircase error; with the mass source planted out it is not;
+* the hybrid LV inlet opens and closes once per beat on the axisymmetric
+  tube.
+"""
+import numpy as np
+import pytest
+from scipy import special
+
+import oracle.axisym as ax
+from workloads import axisym as axw
+from workloads.spec import BC_PRESSURE, BC_VELOCITY, Boundary
+
+
+def test_rest_stays_at_rest():
+    node, _ = axw.stenosis(10, 24, 8.0, 3.0, 5.0)
+    o = ax.AxiOracle(node, 0.7, [Boundary(BC_PRESSURE, 0, +1, [0.0]), Boundary(BC_PRESSURE, 0, -1, [0.0])])
+    o.step(50)
+    P, ux, ur = o.fields()
+    fl = o.fluid
+    assert np.abs(P[fl] - ax.PREF).max() < 1e-15 and np.abs(ux).max() < 1e-15 and np.abs(ur).max() < 1e-15
+
+
+def test_hagen_poiseuille_second_order():
+    tau, G = 0.8, 1e-6
+    nu = (tau - 0.5) / 3
+    errs = []
+    for R in (5, 10, 20):
+        o = ax.AxiOracle(np.zeros((R, 1), np.uint8), tau, periodic_x=True, body_force=G)
+        o.step(int(6 * R * R / nu))
+        r = np.arange(R) + 0.5
+        ua = G / (4 * nu) * (R * R - r * r)
+        errs.append(np.abs(o.fields()[1][:, 0] - ua).max() / ua.max())
+    assert errs[0] < 6e-3
+    assert all(3.8 < errs[i] / errs[i + 1] < 4.2 for i in range(2)), errs
+
+
+def test_womersley_second_order():
+    tau, G0, alpha = 0.8, 1e-6, 3.0
+    nu = (tau - 0.5) / 3
+    i32 = np.exp(0.75j * np.pi)
+    errs = []
+    for R in (4, 8, 16):
+        w = (alpha / R) ** 2 * nu
+        T = 2 * np.pi / w
+        o = ax.AxiOracle(np.zeros((R, 1), np.uint8), tau, periodic_x=True)
+        r = np.arange(R) + 0.5
+        U = G0 / (1j * w) * (1 - special.jv(0, i32 * alpha * r / R) / special.jv(0, i32 * alpha))
+        err = mx = 0.0
+        for n in range(int(5 * T)):
+            o.G = G0 * np.cos(w * n)
+            o.step(1)
+            if n > 4 * T:
+                o.G = G0 * np.cos(w * (n + 1))
+                ua = (U * np.exp(1j * w * (n + 1))).real
+                err = max(err, np.abs(o.fields()[1][:, 0] - ua).max())
+                mx = max(mx, np.abs(ua).max())
+        errs.append(err / mx)
+    assert errs[0] < 2e-2
+    assert errs[0] / errs[1] > 3.2 and errs[1] / errs[2] > 3.5, errs
+
+
+def _stenosis_flux_spread(plant_no_mass_source: bool):
+    node, _ = axw.stenosis(12, 64, 10.0, 4.0, 8.0)
+    n_in = int((node[:, 0] == 2).sum())
+    r = np.arange(n_in) + 0.5
+    prof = np.zeros((n_in, 3))
+    prof[:, 0] = 0.02 * (1 - (r / 10.0) ** 2)
+    bcs = [Boundary(BC_VELOCITY, 0, +1, [0.0], profile=prof), Boundary(BC_PRESSURE, 0, -1, [0.0])]
+    o = ax.AxiOracle(node, 1.0, bcs)
+    if plant_no_mass_source:
+        def no_mass(self, _orig=ax.AxiOracle._macros):
+            _orig(self)
+            self.m[:] = 0.0
+            self.P = ax.CS2 * self.sf
+        o._macros = no_mass.__get__(o)
+    o.step(12000)
+    ux = o.fields()[1]
+    rr = (np.arange(o.nr) + 0.5)[:, None]
+    Q = (2 * np.pi * rr * ux * o.fluid).sum(axis=0)[1:-1]
+    return (Q.max() - Q.min()) / Q.mean()
+
+
+def test_flow_rate_conserved_through_stenosis():
+    assert _stenosis_flux_spread(False) < 0.03      # 2.2 %; 0.58 % at twice the resolution
+    assert _stenosis_flux_spread(True) > 0.3        # mass source planted out: 43 %
+
+
+def test_lv_inlet_cycles_on_axisymmetric_tube():
+    inst = axw.lv_tube(nr=8, nx=40, period=600)
+    o = ax.AxiOracle(inst.node, inst.tau, inst.boundaries)
+    o.step(1800)
+    w = o.waves()
+    valve = w[:, 4]
+    opens = int((np.diff(valve) > 0).sum())
+    closes = int((np.diff(valve) < 0).sum())
+    assert opens >= 2 and closes >= 2
+    # while the valve is open the inlet pressure follows the ventricle (pressure-type coupling)
+    assert np.abs(w[valve == 1, 2]).max() > 0
