@@ -14,8 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 SO = os.path.join(BUILD, "liblbm.so")
-SOURCES = ["lbm_api.cu", "lbm_stream_collide.cu", "lbm_kernels.cu", "lbm_ib.cu", "lbm_layout.cu", "lbm_noalloc.cu", "lbm_mlp.cu"]
-HEADERS = ["lbm_internal.h", "lbm_kernels.h", "lbm_device.cuh"]
+SOURCES = ["lbm_api.cu", "lbm_stream_collide.cu", "lbm_kernels.cu", "lbm_axi.cu", "lbm_ib.cu", "lbm_layout.cu", "lbm_noalloc.cu", "lbm_mlp.cu"]
+HEADERS = ["lbm_internal.h", "lbm_kernels.h", "lbm_device.cuh", "lbm_zero_d.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-O2"]

@@ -34,8 +34,9 @@ def test_every_declared_symbol_is_exported(lib):
     assert len(names) >= 15
     for n in names:
         assert hasattr(lib, n), n
-    from paper_2112_05258_gb300 import lbm, mlp
-    assert sorted(lbm.EXPORTS + mlp.EXPORTS) == names
+    from paper_2112_05258_gb300 import axisym, lbm, mlp
+    assert sorted(lbm.EXPORTS + mlp.EXPORTS + axisym.EXPORTS) == names
+    axisym.load()
 
 
 def _cfg(lbm, node, tau=0.8, bcs=(), precision=0, graph_steps=0):
@@ -90,3 +91,25 @@ def test_create_rejects_invalid_configs(lib):
     node2[5, 5, 5] = 9
     cfg, keep = _cfg(lbm, node2, bcs=(vel, rcr))
     assert _create(lib, cfg) == -1
+
+
+def test_axisymmetric_create_rejects_invalid_configs(lib):
+    # validation happens before any CUDA call
+    from paper_2112_05258_gb300 import LBMError, axisym
+    from workloads import axisym as axw
+    axisym.load()
+    good = axw.lv_tube()
+    for mutate in ("tau", "column", "code"):
+        inst = axw.lv_tube()
+        node = inst.node.copy()
+        if mutate == "tau":
+            inst.tau = 0.5
+        elif mutate == "column":
+            node[2, 5] = 2                 # a boundary node off its column
+        else:
+            node[2, 5] = 7                 # a code without a boundary
+        inst.node = node
+        with pytest.raises(LBMError) as e:
+            axisym.AxiLattice(inst)
+        assert e.value.status == -1        # LBM_ERR_ARG, not a CUDA failure
+    assert good.node.shape == (8, 40)

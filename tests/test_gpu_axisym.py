@@ -1,0 +1,113 @@
+"""Axisymmetric lattice on the GPU (liblbm through include/lbm_axi.h) against
+the axisymmetric CPU oracle on identical inputs.
+
+FP64 instantiation: populations, fields, waveforms and 0D states agree to
+rounding (1e-12 on f ~ 1/9) for a Womersley inlet with an RCR outlet, the
+hybrid LV inlet through several valve cycles, and a stenosis with radial
+velocities (links across the axis, mass source active), from rest and from
+seeded random populations.  FP32: waveforms within 1e-4 of their peak.
+"""
+import numpy as np
+import pytest
+
+from oracle.axisym import AxiOracle
+from workloads import axisym as axw
+from workloads.spec import BC_PRESSURE, BC_RCR, BC_VELOCITY, Boundary
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Axi():
+    from paper_2112_05258_gb300 import load
+    from paper_2112_05258_gb300.axisym import AxiLattice
+    load()
+    return AxiLattice
+
+
+def _stenosis_case(outlet="pressure"):
+    node, _ = axw.stenosis(12, 40, 10.0, 4.0, 6.0)
+    n_in = int((node[:, 0] == 2).sum())
+    r = np.arange(n_in) + 0.5
+    prof = np.zeros((n_in, 3))
+    prof[:, 0] = 0.03 * (1 - (r / 10.0) ** 2)
+    prof[:, 1] = 0.01
+    out = Boundary(BC_PRESSURE, 0, -1, [1e-4]) if outlet == "pressure" else Boundary(BC_RCR, 0, -1, [0.05, 200.0, 1.0, 0.0])
+    return axw.AxiInstance(node=node, tau=0.7, name="axi_stenosis",
+                           boundaries=[Boundary(BC_VELOCITY, 0, +1, [2 * np.pi / 200], profile=prof), out])
+
+
+def _compare(lat, o, atol_f=1e-12, atol_w=1e-12):
+    fl = o.fluid
+    fg, fo = lat.populations(), o.populations()
+    assert np.abs(fg[:, fl] - fo[:, fl]).max() < atol_f
+    for a, b in zip(lat.fields(), o.fields()):
+        assert np.abs(a[fl] - b[fl]).max() < atol_f
+    wg, wo = lat.waves(), o.waves()
+    assert wg.shape == wo.shape
+    assert np.array_equal(wg[:, 0], wo[:, 0])
+    assert np.abs(wg[:, 1:] - wo[:, 1:]).max() < atol_w
+    for k in range(len(o.bcs)):
+        sg, so = lat.state_0d(k), o.state_0d(k)
+        assert sg[6] == so["valve"]
+        if o.bcs[k]["kind"] == 2:                       # LV: closure time
+            assert sg[7] == so["Td"]
+        assert abs(sg[2] - so["Qu"]) < atol_w and abs(sg[3] - (so["Pbar"] - 1 / 3)) < atol_w
+
+
+def _run(Axi, inst, steps, f0=None, prec="f64", **kw):
+    lat = Axi(inst, precision=prec, **kw)
+    o = AxiOracle(inst.node, inst.tau, inst.boundaries, q_scale=inst.q_scale)
+    if f0 is not None:
+        lat.init_populations(f0)
+        o.set_populations(f0)
+    lat.step(steps)
+    lat.sync()
+    o.step(steps)
+    return lat, o
+
+
+def test_f64_womersley_rcr(Axi):
+    lat, o = _run(Axi, axw.womersley_tube(), 300)
+    _compare(lat, o)
+
+
+def test_f64_lv_inlet_cycles(Axi):
+    inst = axw.lv_tube(period=600)
+    lat, o = _run(Axi, inst, 1500)
+    w = o.waves()
+    assert (np.diff(w[:, 4]) < 0).sum() >= 2
+    _compare(lat, o, 1e-11, 1e-11)
+
+
+def test_f64_stenosis_radial_flow(Axi):
+    lat, o = _run(Axi, _stenosis_case(), 400)
+    assert np.abs(o.fields()[2]).max() > 1e-4           # radial velocities present
+    _compare(lat, o)
+
+
+def test_f64_random_start(Axi):
+    inst = _stenosis_case("rcr")
+    rng = np.random.default_rng(5)
+    f0 = (np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+          * (1 + 1e-2 * rng.standard_normal((9,) + inst.node.shape)))
+    lat, o = _run(Axi, inst, 150, f0=f0)
+    _compare(lat, o)
+
+
+def test_graph_equals_direct(Axi):
+    inst = axw.lv_tube(period=300)
+    g = Axi(inst, precision="f64", graph_steps=8)
+    g.step(203)
+    d = Axi(inst, precision="f64", graph_steps=1000)
+    d.step(203)
+    assert np.array_equal(g.populations(), d.populations())
+    assert np.array_equal(g.waves(), d.waves())
+
+
+def test_f32_womersley_waveforms(Axi):
+    inst = axw.womersley_tube()
+    lat, o = _run(Axi, inst, 3000, prec="f32")
+    wg, wo = lat.waves(), o.waves()
+    for col in (1, 2, 5, 6):
+        assert np.abs(wg[:, col] - wo[:, col]).max() < 1e-4 * np.abs(wo[:, col]).max() + 1e-9
