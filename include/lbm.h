@@ -186,6 +186,12 @@ lbm_status lbm_sync(lbm_handle *h);
  * (Eqs. rho, v before the force term of step n is added). */
 lbm_status lbm_read_fields(lbm_handle *h, int inst, double *P, double *jx, double *jy, double *jz);
 
+/* The same fields written as FP32 into caller-owned DEVICE arrays of
+ * nx*ny*nz floats each (box order, non-fluid 0), e.g. torch tensors on the
+ * handle's device.  Stream-ordered on the handle's stream and asynchronous:
+ * the arrays are complete once that stream reaches this point. */
+lbm_status lbm_read_fields_device(lbm_handle *h, int inst, float *P, float *jx, float *jy, float *jz);
+
 /* Host output: f_i(x, t_n) as 19 x (nx*ny*nz) doubles (non-fluid 0). */
 lbm_status lbm_read_populations(lbm_handle *h, int inst, double *f);
 
@@ -218,6 +224,22 @@ lbm_status lbm_wall_shear(lbm_handle *h, int inst, double *wss);
  * 1/3 at rest), v the velocity.  Used to start from a predicted state. */
 lbm_status lbm_init_equilibrium(lbm_handle *h, int inst, const double *P, const double *vx, const double *vy,
                                 const double *vz);
+
+/* Checkpoint and exact resume.  lbm_checkpoint_size gives the bytes of a
+ * checkpoint of the whole handle: the resident populations (with the ghost
+ * populations of the next step), the force density of the last step, both
+ * slots of every 0D state, the closure velocities, the waveform ring, the
+ * wall-node arrays (X, V_s, penalty integral, force, interpolated velocity),
+ * the step counter and the status word, behind a header with the layout
+ * sizes.  lbm_checkpoint_save copies it into a host buffer of that size
+ * (waits for the stream); lbm_checkpoint_load restores it into a handle
+ * created from the same configuration (the header is checked:
+ * LBM_ERR_ARG on a mismatch or a short buffer), after which stepping
+ * continues the saved trajectory exactly (up to the order of the
+ * immersed-boundary float atomics). */
+lbm_status lbm_checkpoint_size(lbm_handle *h, int64_t *bytes);
+lbm_status lbm_checkpoint_save(lbm_handle *h, void *buf, int64_t bytes);
+lbm_status lbm_checkpoint_load(lbm_handle *h, const void *buf, int64_t bytes);
 
 /* Overwrites the 0D state of boundary bc of instance inst with
  * {P_w (RCR) or P_v (LV) gauge pressure, valve_open (0 or 1), T_d}. */

@@ -58,6 +58,7 @@ struct lbm_handle {
     double *fil_par = nullptr;
     uint64_t *ibmask = nullptr;
     double *rd_f19 = nullptr, *rd_mac = nullptr;  // read-out scratch, largest instance (allocated on first use)
+    int32_t *cell_box_dev = nullptr;               // box index of every stored cell (allocated on first use)
     int64_t max_inst_cells = 0;
     int variant = 0;  // stream-collide occupancy variant (see launch_stream_collide)
     int *inst_bc = nullptr;  // per instance: bc_first, n_bc
@@ -583,6 +584,25 @@ lbm_status lbm_read_fields(lbm_handle *h, int inst, double *P, double *jx, doubl
     return LBM_OK;
 }
 
+lbm_status lbm_read_fields_device(lbm_handle *h, int inst, float *P, float *jx, float *jy, float *jz) {
+    if (bad_inst(h, inst) || !P || !jx || !jy || !jz) return fail(h, LBM_ERR_ARG, "bad instance or array");
+    CK(h, cudaSetDevice(h->device));
+    const Layout &L = h->L;
+    if (!h->cell_box_dev) {
+        std::vector<int32_t> box(L.cell_box.begin(), L.cell_box.end());
+        CK(h, upload(h, &h->cell_box_dev, box));
+    }
+    if (!h->rd_mac) CK(h, dalloc(h, &h->rd_mac, 4 * (size_t)h->max_inst_cells));
+    const int64_t c0 = L.inst_cell_begin[inst], c1 = L.inst_cell_end[inst];
+    const lbm_instance_desc &d = h->inst[inst];
+    const size_t nbox = (size_t)d.nx * d.ny * d.nz;
+    float *outs[4] = {P, jx, jy, jz};
+    for (float *o : outs) CK(h, cudaMemsetAsync(o, 0, nbox * sizeof(float), h->stream));
+    CK(h, launch_gather(h->prec, h->f[h->parity], h->kp, (int)c0, (int)c1, nullptr, h->rd_mac, h->stream));
+    CK(h, launch_scatter_box(h->rd_mac, (int)(c1 - c0), h->cell_box_dev + c0, P, jx, jy, jz, h->stream));
+    return LBM_OK;
+}
+
 lbm_status lbm_read_populations(lbm_handle *h, int inst, double *f) {
     if (bad_inst(h, inst) || !f) return fail(h, LBM_ERR_ARG, "bad instance or array");
     CK(h, cudaSetDevice(h->device));
@@ -745,6 +765,97 @@ lbm_status lbm_init_equilibrium(lbm_handle *h, int inst, const double *P, const 
     CK(h, cudaMemcpy(h->rd_mac, host.data(), host.size() * sizeof(double), cudaMemcpyHostToDevice));
     CK(h, launch_init_eq(h->prec, h->f[h->parity], h->kp, h->rd_mac, (int)c0, (int)c1, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
+    return LBM_OK;
+}
+
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int64_t version, prec, n_stored, n_bc, n_ib, n_xf, wave_cap, steps, parity;
+};
+struct CkptSection {
+    void *dev;
+    size_t bytes;
+};
+std::vector<CkptSection> ckpt_sections(lbm_handle *h) {
+    const Layout &L = h->L;
+    const size_t n = (size_t)L.n_stored, nb = L.bc.size(), ns = L.ib_dA.size();
+    std::vector<CkptSection> v = {
+        {h->f[h->parity], (size_t)NQ * n * h->sbytes},
+        {h->b, 4 * n * (size_t)h->rbytes},
+        {h->bc_state, 2 * std::max<size_t>(nb, 1) * sizeof(BcState)},
+        {h->v0, 3 * std::max<size_t>(1, L.xf.size()) * sizeof(double)},
+        {h->wave, (size_t)h->wave_cap * std::max<size_t>(1, nb) * 4 * sizeof(double)},
+        {h->step_dev, sizeof(long long)},
+        {h->status, sizeof(unsigned)},
+    };
+    if (ns) {
+        double *ib[5] = {h->ibX, h->ibVs, h->ibI, h->ibF, h->ibVf};
+        for (double *a : ib) v.push_back({a, 3 * ns * sizeof(double)});
+    }
+    return v;
+}
+CkptHeader ckpt_header(const lbm_handle *h) {
+    CkptHeader hd;
+    memset(&hd, 0, sizeof hd);
+    memcpy(hd.magic, "LBMCKPT1", 8);
+    hd.version = 1;
+    hd.prec = h->prec;
+    hd.n_stored = h->L.n_stored;
+    hd.n_bc = (int64_t)h->L.bc.size();
+    hd.n_ib = (int64_t)h->L.ib_dA.size();
+    hd.n_xf = (int64_t)h->L.xf.size();
+    hd.wave_cap = h->wave_cap;
+    hd.steps = h->steps;
+    hd.parity = h->parity;
+    return hd;
+}
+}  // namespace
+
+lbm_status lbm_checkpoint_size(lbm_handle *h, int64_t *bytes) {
+    if (!h || !bytes) return fail(h, LBM_ERR_ARG, "bad arguments");
+    size_t total = sizeof(CkptHeader);
+    for (auto &sct : ckpt_sections(h)) total += sct.bytes;
+    *bytes = (int64_t)total;
+    return LBM_OK;
+}
+
+lbm_status lbm_checkpoint_save(lbm_handle *h, void *buf, int64_t bytes) {
+    int64_t need = 0;
+    if (!h || !buf || lbm_checkpoint_size(h, &need) != LBM_OK || bytes < need)
+        return fail(h, LBM_ERR_ARG, "null buffer or smaller than lbm_checkpoint_size");
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    uint8_t *p = static_cast<uint8_t *>(buf);
+    const CkptHeader hd = ckpt_header(h);
+    memcpy(p, &hd, sizeof hd);
+    p += sizeof hd;
+    for (auto &sct : ckpt_sections(h)) {
+        CK(h, cudaMemcpy(p, sct.dev, sct.bytes, cudaMemcpyDeviceToHost));
+        p += sct.bytes;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_checkpoint_load(lbm_handle *h, const void *buf, int64_t bytes) {
+    int64_t need = 0;
+    if (!h || !buf || lbm_checkpoint_size(h, &need) != LBM_OK || bytes < need)
+        return fail(h, LBM_ERR_ARG, "null buffer or smaller than lbm_checkpoint_size");
+    CkptHeader hd, mine = ckpt_header(h);
+    memcpy(&hd, buf, sizeof hd);
+    if (memcmp(hd.magic, mine.magic, 8) != 0 || hd.version != mine.version || hd.prec != mine.prec ||
+        hd.n_stored != mine.n_stored || hd.n_bc != mine.n_bc || hd.n_ib != mine.n_ib || hd.n_xf != mine.n_xf ||
+        hd.wave_cap != mine.wave_cap || (hd.parity != 0 && hd.parity != 1) || hd.steps < 0)
+        return fail(h, LBM_ERR_ARG, "checkpoint does not match this handle's configuration");
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->parity = (int)hd.parity;  // selects the resident buffer the sections refer to
+    h->steps = hd.steps;
+    const uint8_t *p = static_cast<const uint8_t *>(buf) + sizeof hd;
+    for (auto &sct : ckpt_sections(h)) {
+        CK(h, cudaMemcpy(sct.dev, p, sct.bytes, cudaMemcpyHostToDevice));
+        p += sct.bytes;
+    }
     return LBM_OK;
 }
 

@@ -55,6 +55,31 @@ struct Params {
     void *aux;             // 6 x n compute type at first-layer nodes: s_sum + m/2, j_x, j_r, v_x, v_r, s_sum
     double tau;
     unsigned *status;
+    // relaxation constants and 1/r per row in both arithmetic types (no
+    // division or FP64 conversion per node): omega = 1/tau, k = 1 - 1/(2 tau),
+    // nu = (tau - 1/2)/3
+    float omega_f, k_f, nu_f;
+    double omega_d, k_d, nu_d;
+    const float *inv_r_f;
+    const double *inv_r_d;
+};
+
+template <class R> struct Consts;
+template <> struct Consts<float> {
+    static __device__ __forceinline__ void get(const Params &p, int j, float *om, float *k, float *nu, float *ir) {
+        *om = p.omega_f;
+        *k = p.k_f;
+        *nu = p.nu_f;
+        *ir = __ldg(&p.inv_r_f[j]);
+    }
+};
+template <> struct Consts<double> {
+    static __device__ __forceinline__ void get(const Params &p, int j, double *om, double *k, double *nu, double *ir) {
+        *om = p.omega_d;
+        *k = p.k_d;
+        *nu = p.nu_d;
+        *ir = __ldg(&p.inv_r_d[j]);
+    }
 };
 
 struct BcDev {
@@ -75,22 +100,24 @@ struct BcDev {
     long long *step;                        // steps done
 };
 
+// grid: (ceil(nx / 256), nr), one row of the (x, r) grid per blockIdx.y
 template <class S>
 __global__ void __launch_bounds__(256) k_axi_collide(const S *__restrict__ fin, S *__restrict__ fout, Params p) {
     using R = typename Storage<S>::R;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= p.n) return;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (x >= p.nx) return;
+    const int c = j * p.nx + x;
     const uint32_t fl = __ldg(&p.flags[c]);
     if (!(fl & AF_FLUID)) return;
-    const int n = p.n, x = c % p.nx, j = c / p.nx;
+    const int n = p.n;
     R s[Q9];
 #pragma unroll
     for (int i = 0; i < Q9; i++) {
-        int src;
-        if (i == 0) src = c;
-        else if (fl & (1u << i)) src = opp(i) * n + c;
-        else if (j - er(i) < 0) src = mir(i) * n + (x - ex(i));  // mirror at the axis (row 0)
-        else src = i * n + c - ex(i) - er(i) * p.nx;
+        uint32_t src;
+        if (i == 0) src = (uint32_t)c;
+        else if (fl & (1u << i)) src = (uint32_t)(opp(i) * n + c);
+        else if (j - er(i) < 0) src = (uint32_t)(mir(i) * n + (x - ex(i)));  // mirror at the axis (row 0)
+        else src = (uint32_t)(i * n + c - ex(i) - er(i) * p.nx);
         s[i] = Storage<S>::ld(fin + src);
     }
     R sd = 0, jx = 0, jr = 0, pxr = 0, prr = 0;
@@ -104,8 +131,8 @@ __global__ void __launch_bounds__(256) k_axi_collide(const S *__restrict__ fin, 
         }
         if (ex(i) * er(i)) pxr += R(ex(i) * er(i)) * s[i];
     }
-    const R tau = (R)p.tau, k = R(1) - R(0.5) / tau, omega = R(1) / tau, nu = (tau - R(0.5)) / R(3);
-    const R inv_r = R(1) / (R(j) + R(0.5));
+    R omega, k, nu, inv_r;
+    Consts<R>::get(p, j, &omega, &k, &nu, &inv_r);
     const R m = -jr * inv_r;
     const R sp = sd + R(0.5) * m;                       // 3P - 1
     // non-equilibrium stress of f against f^eq(P, j): Pi^eq_xr = j_x j_r, Pi^eq_rr = P + j_r^2
@@ -133,7 +160,7 @@ __global__ void __launch_bounds__(256) k_axi_collide(const S *__restrict__ fin, 
         const R eg = R(ex(i)) * gx + R(er(i)) * gr;
         const R seq = w * (sp + R(3) * eu + R(4.5) * eu * eu - usq);
         const R post = s[i] - omega * (s[i] - seq) + k * w * (R(3) * (eg - vg) + R(9) * eu * eg) + k * w * m;
-        Storage<S>::st(fout + (size_t)i * n + c, post);
+        Storage<S>::st(fout + ((uint32_t)i * (uint32_t)n + (uint32_t)c), post);  // 9 n < 2^31
     }
 }
 
@@ -310,6 +337,8 @@ struct lbm_axi_handle {
     unsigned *status = nullptr;
     long long *d_step = nullptr;
     double *rd = nullptr;  // read-out scratch (12 n doubles)
+    float *inv_r_f = nullptr;
+    double *inv_r_d = nullptr;
     // boundaries (host copies kept for read-out)
     std::vector<BcParam> bcp;
     std::vector<double> etab_h;
@@ -356,12 +385,20 @@ Params params(const lbm_axi_handle *h) {
     p.aux = h->aux;
     p.tau = h->tau;
     p.status = h->status;
+    p.omega_d = 1.0 / h->tau;
+    p.k_d = 1.0 - 0.5 / h->tau;
+    p.nu_d = (h->tau - 0.5) / 3.0;
+    p.omega_f = (float)p.omega_d;
+    p.k_f = (float)p.k_d;
+    p.nu_f = (float)p.nu_d;
+    p.inv_r_f = h->inv_r_f;
+    p.inv_r_d = h->inv_r_d;
     return p;
 }
 
 cudaError_t launch_step(lbm_axi_handle *h) {
     const Params p = params(h);
-    const int grid = (h->n + 255) / 256;
+    const dim3 grid((h->nx + 255) / 256, h->nr);
     void *fin = h->f[h->parity], *fout = h->f[1 - h->parity];
     if (h->prec == LBM_F64) {
         k_axi_collide<double><<<grid, 256, 0, h->stream>>>(static_cast<const double *>(fin), static_cast<double *>(fout), p);
@@ -555,6 +592,16 @@ lbm_status lbm_axi_create(const lbm_axi_config *cfg, lbm_axi_handle **out) {
         cudaMemset(h->d_step, 0, sizeof(long long)) != cudaSuccess || aalloc(h, &h->rd, (size_t)12 * n) != cudaSuccess)
         return bail("out of memory");
     h->aux = aq;
+    {
+        std::vector<double> ird(nr);
+        std::vector<float> irf(nr);
+        for (int j = 0; j < nr; j++) {
+            ird[j] = 1.0 / (j + 0.5);
+            irf[j] = (float)(1.0 / (j + 0.5));
+        }
+        if (aupload(h, &h->inv_r_d, ird) != cudaSuccess || aupload(h, &h->inv_r_f, irf) != cudaSuccess)
+            return bail("out of memory");
+    }
     h->bcp = bcp;
     h->etab_h = etab;
     BcDev &bd = h->bd;

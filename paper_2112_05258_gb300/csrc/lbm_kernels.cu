@@ -378,6 +378,25 @@ cudaError_t launch_gather(int prec, const void *fin, const KParams &p, int c0, i
     return cudaGetLastError();
 }
 
+// compact -> box scatter of the gathered P, j into FP32 device arrays
+__global__ void k_scatter_box(const double *__restrict__ mac4, int M, const int32_t *__restrict__ box, float *P,
+                              float *jx, float *jy, float *jz) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    const int b = box[m];
+    P[b] = (float)mac4[m];
+    jx[b] = (float)mac4[M + m];
+    jy[b] = (float)mac4[2 * (size_t)M + m];
+    jz[b] = (float)mac4[3 * (size_t)M + m];
+}
+
+cudaError_t launch_scatter_box(const double *mac4, int M, const int32_t *box, float *P, float *jx, float *jy,
+                               float *jz, cudaStream_t s) {
+    if (M == 0) return cudaSuccess;
+    k_scatter_box<<<(M + 255) / 256, 256, 0, s>>>(mac4, M, box, P, jx, jy, jz);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_wall_shear(int prec, const void *fin, const KParams &p, int c0, int c1, double *out3,
                               cudaStream_t s) {
     const int block = 128;

@@ -127,7 +127,7 @@ def main(argv=None):
     ap.add_argument("--out", default=None)
     a = ap.parse_args(argv)
     report = {}
-    for case in a.cases.split(","):
+    for case in [c for c in a.cases.split(",") if c]:
         res = [run(case, int(n), a.precision) for n in a.resolutions.split(",")]
         errors(res)
         for r in res:

@@ -70,7 +70,8 @@ EXPORTS = ["lbm_create", "lbm_set_0d_params", "lbm_init_populations", "lbm_step"
            "lbm_read_ib", "lbm_set_ib_state", "lbm_set_kernel_timing", "lbm_get_kernel_time",
            "lbm_get_info", "lbm_last_error", "lbm_destroy", "lbm_boundary_flux_noalloc",
            "lbm_init_equilibrium", "lbm_set_0d_state", "lbm_cycle_change", "lbm_autotune",
-           "lbm_wall_shear", "lbm_check_config"]
+           "lbm_wall_shear", "lbm_check_config", "lbm_checkpoint_size", "lbm_checkpoint_save",
+           "lbm_checkpoint_load", "lbm_read_fields_device"]
 
 _lib = None
 
@@ -106,6 +107,10 @@ def load(path: Optional[str] = None):
     L.lbm_destroy.restype = None
     L.lbm_init_equilibrium.argtypes = [H, ctypes.c_int, _dp, _dp, _dp, _dp]
     L.lbm_wall_shear.argtypes = [H, ctypes.c_int, _dp]
+    L.lbm_checkpoint_size.argtypes = [H, ctypes.POINTER(ctypes.c_int64)]
+    L.lbm_read_fields_device.argtypes = [H, ctypes.c_int] + [ctypes.c_void_p] * 4
+    L.lbm_checkpoint_save.argtypes = [H, ctypes.c_void_p, ctypes.c_int64]
+    L.lbm_checkpoint_load.argtypes = [H, ctypes.c_void_p, ctypes.c_int64]
     L.lbm_check_config.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(LayoutStats), ctypes.c_char_p,
                                    ctypes.c_int]
     L.lbm_set_0d_state.argtypes = [H, ctypes.c_int, ctypes.c_int, _dp]
@@ -324,6 +329,24 @@ class Lattice:
         out = np.empty((nx * ny * nz, 3))
         self._ck(load().lbm_wall_shear(self._h, inst, _p(out)))
         return out
+
+    def fields_device(self, inst: int, P: int, jx: int, jy: int, jz: int):
+        """Writes P and j of f(t_n) as FP32 into caller-owned device arrays of
+        nx*ny*nz floats (raw device pointers, e.g. tensor.data_ptr()),
+        ordered on the lattice's stream."""
+        self._ck(load().lbm_read_fields_device(self._h, inst, *(ctypes.c_void_p(int(a)) for a in (P, jx, jy, jz))))
+
+    def checkpoint(self) -> np.ndarray:
+        """The whole device state as a byte array (exact resume with restore)."""
+        n = ctypes.c_int64()
+        self._ck(load().lbm_checkpoint_size(self._h, ctypes.byref(n)))
+        buf = np.empty(n.value, dtype=np.uint8)
+        self._ck(load().lbm_checkpoint_save(self._h, buf.ctypes.data_as(ctypes.c_void_p), n.value))
+        return buf
+
+    def restore(self, buf: np.ndarray):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        self._ck(load().lbm_checkpoint_load(self._h, buf.ctypes.data_as(ctypes.c_void_p), buf.size))
 
     def init_equilibrium(self, inst: int, P, vx, vy, vz):
         arrs = [np.ascontiguousarray(a, dtype=np.float64).reshape(-1) for a in (P, vx, vy, vz)]

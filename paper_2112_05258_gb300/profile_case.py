@@ -8,7 +8,8 @@ about 0.4 GB of FP32 populations: larger than L2, small enough for a
 multi-pass capture).  ``aorta``: the full-size elastic-wall workload.
 ``fil_tube``: elastic tube 64 x 64 x 512 whose membrane (radius 24, 151 x 510
 nodes) is also 151 axial SGFD filaments; ``spring_tube``: the same membrane
-without the filaments.
+without the filaments.  ``axi``: the axisymmetric straight aorta at 512
+nodes per diameter (12802 x 256 = 3.3M nodes, 236 MB of FP32 populations).
 Steps are launched directly (no CUDA graph) so that each kernel launch is
 visible to a profiler.
 """
@@ -24,13 +25,25 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="tube", choices=["tube", "aorta", "fil_tube", "spring_tube"])
+    ap.add_argument("--case", default="tube", choices=["tube", "aorta", "fil_tube", "spring_tube", "axi"])
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--precision", default="f32")
     ap.add_argument("--block", type=int, default=0)
     args = ap.parse_args()
     from paper_2112_05258_gb300 import Lattice
     from workloads import aorta, configs
+    if args.case == "axi":
+        from paper_2112_05258_gb300.axisym import AxiLattice
+        from workloads import axisym
+        inst = axisym.straight_aorta(512)
+        lat = AxiLattice(inst, precision=args.precision, graph_steps=2 * (args.steps + 1))
+        t0 = time.perf_counter()
+        lat.step(args.steps)
+        lat.sync()
+        print(f"axi {args.precision}: nodes {inst.node.size} steps {args.steps} in "
+              f"{(time.perf_counter() - t0) * 1e3:.1f} ms")
+        lat.close()
+        return
     if args.case == "tube":
         inst = configs.rigid_tube(128, 128, 512, radius=40.0, period=4000)
     elif args.case in ("fil_tube", "spring_tube"):

@@ -249,3 +249,18 @@ def test_ib_kernel_variants_agree(Lattice):
         assert np.abs(lat.populations(0) - ref.populations(0)).max() < 1e-13
         for a, b in zip(lat.ib_state(0, n), ref.ib_state(0, n)):
             assert np.abs(a - b).max() < 1e-13
+
+
+def test_fields_device_matches_host(Lattice):
+    torch = pytest.importorskip("torch")
+    inst = configs.lv_tube(period=300)
+    lat = Lattice([inst], precision="f32")
+    lat.step(250)
+    nz, ny, nx = inst.node.shape
+    outs = [torch.full((nz * ny * nx,), 7.0, dtype=torch.float32, device="cuda:0") for _ in range(4)]
+    torch.cuda.synchronize()
+    lat.fields_device(0, *(t.data_ptr() for t in outs))
+    lat.sync()
+    host = lat.fields(0)
+    for t, h in zip(outs, host):
+        assert np.array_equal(t.cpu().numpy(), h.astype(np.float32))
