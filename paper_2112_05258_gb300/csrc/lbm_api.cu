@@ -273,7 +273,7 @@ lbm_status lbm_check_config(const lbm_config *cfg, lbm_layout_stats *stats, char
     Layout L;
     if (st == LBM_OK) {
         msg = build_layout(cfg, L);
-        if (msg.empty() && (double)NQ * (double)L.n_stored >= 2147483647.0)
+        if (msg.empty() && (double)NQ * (double)population_cells(L.n_stored) >= 2147483647.0)
             msg = "more than 2^31 / 19 stored cells (32-bit population offsets)";
         st = msg.empty() ? LBM_OK : LBM_ERR_ARG;
     }
@@ -328,7 +328,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
     std::string e = build_layout(cfg, h->L);
     if (!e.empty()) return bail(LBM_ERR_ARG, e);
     Layout &L = h->L;
-    if ((double)NQ * (double)L.n_stored >= 2147483647.0)
+    if ((double)NQ * (double)population_cells(L.n_stored) >= 2147483647.0)
         return bail(LBM_ERR_ARG, "more than 2^31 / 19 stored cells (32-bit population offsets)");
     if (cudaSetDevice(h->device) != cudaSuccess) return bail(LBM_ERR_CUDA, "cudaSetDevice failed");
     if (cfg->stream) {
@@ -346,8 +346,9 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
     };
     bool ok = true;
     for (int k = 0; k < 2 && ok; k++) {
-        ok = ck(dalloc_bytes(h, &h->f[k], (size_t)NQ * n * h->sbytes), "populations");
-        if (ok) ok = ck(cudaMemset(h->f[k], 0, (size_t)NQ * n * h->sbytes), "memset");
+        const size_t pop_bytes = (size_t)NQ * (size_t)population_cells((int64_t)n) * h->sbytes;
+        ok = ck(dalloc_bytes(h, &h->f[k], pop_bytes), "populations");
+        if (ok) ok = ck(cudaMemset(h->f[k], 0, pop_bytes), "memset");
     }
     if (ok) ok = ck(dalloc_bytes(h, &h->b, 4 * n * h->rbytes), "b") && ck(cudaMemset(h->b, 0, 4 * n * h->rbytes), "memset");
     if (ok) ok = ck(dalloc_bytes(h, &h->aux, 4 * n * h->rbytes), "aux") && ck(cudaMemset(h->aux, 0, 4 * n * h->rbytes), "memset");
@@ -781,7 +782,7 @@ std::vector<CkptSection> ckpt_sections(lbm_handle *h) {
     const Layout &L = h->L;
     const size_t n = (size_t)L.n_stored, nb = L.bc.size(), ns = L.ib_dA.size();
     std::vector<CkptSection> v = {
-        {h->f[h->parity], (size_t)NQ * n * h->sbytes},
+        {h->f[h->parity], (size_t)NQ * (size_t)population_cells((int64_t)n) * h->sbytes},
         {h->b, 4 * n * (size_t)h->rbytes},
         {h->bc_state, 2 * std::max<size_t>(nb, 1) * sizeof(BcState)},
         {h->v0, 3 * std::max<size_t>(1, L.xf.size()) * sizeof(double)},

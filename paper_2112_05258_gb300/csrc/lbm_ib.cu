@@ -34,8 +34,8 @@ __global__ void k_band_moments(const S *__restrict__ fin, KParams p, IbKParams i
 #pragma unroll
     for (int i = 1; i < NQ; i++) {
         size_t idx;
-        if (fl & (1u << i)) idx = (size_t)opp(i) * N + c;
-        else idx = (size_t)i * N + (size_t)(p.rows[r].nb[nbk(i)] + x - cx(i));
+        if (fl & (1u << i)) idx = pidx(opp(i), (uint32_t)c, (uint32_t)N);
+        else idx = pidx(i, (uint32_t)(p.rows[r].nb[nbk(i)] + x - cx(i)), (uint32_t)N);
         const R fi = Storage<S>::ld(fin + idx);
         if (cx(i)) jx += cx(i) * fi;
         if (cy(i)) jy += cy(i) * fi;

@@ -37,6 +37,24 @@ __host__ __device__ constexpr double wgt(int i) { return i == 0 ? 1.0 / 3.0 : (i
 // index of the neighbour row (y - ey, z - ez) a population i is pulled from
 __host__ __device__ constexpr int nbk(int i) { return (1 - cy(i)) + 3 * (1 - cz(i)); }
 
+// Offset of population i of stored cell c in a population buffer of N cells.
+// Default: structure of arrays, f[i][c].  With LBM_AOSOA = 1: blocks of 32
+// cells holding all 19 populations of the block (f[c / 32][i][c % 32]), so
+// that a warp's reads and writes stay within a few 2.4 KB blocks.  Buffers
+// hold population_cells(N) cells.  19 N < 2^31 keeps offsets in 32 bits.
+#ifndef LBM_AOSOA
+#define LBM_AOSOA 0
+#endif
+__host__ __device__ inline uint32_t pidx(int i, uint32_t c, uint32_t N) {
+#if LBM_AOSOA
+    (void)N;
+    return ((c >> 5) * (uint32_t)NQ + (uint32_t)i) * 32u + (c & 31u);
+#else
+    return (uint32_t)i * N + c;
+#endif
+}
+inline int64_t population_cells(int64_t N) { return LBM_AOSOA ? (N + 31) / 32 * 32 : N; }
+
 // Per-cell flag word: bits 0..18 = the pull source of direction i is a rigid
 // wall (halfway bounce-back: read the opposite population of the own cell).
 enum : uint32_t {

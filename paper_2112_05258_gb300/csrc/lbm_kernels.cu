@@ -164,8 +164,8 @@ __global__ void __launch_bounds__(BC_CHUNK) k_bc_apply(S *__restrict__ f, KParam
     const double us2 = vs[0] * vs[0] + vs[1] * vs[1] + vs[2] * vs[2];
     const double uf2 = vf[0] * vf[0] + vf[1] * vf[1] + vf[2] * vf[2];
     const double dfeq = w * 3.0 * (Ps - Pf) + w * (3.0 * (eus - euf) + 4.5 * (eus * eus - euf * euf) - 1.5 * (us2 - uf2));
-    const double post = (double)Storage<S>::ld(f + (size_t)i * N + cf);
-    Storage<S>::st(f + (size_t)i * N + cb, (R)(post + dfeq));
+    const double post = (double)Storage<S>::ld(f + pidx(i, (uint32_t)cf, (uint32_t)N));
+    Storage<S>::st(f + pidx(i, (uint32_t)cb, (uint32_t)N), (R)(post + dfeq));
 }
 
 // ---------------------------------------------------------------------------
@@ -189,9 +189,9 @@ __global__ void k_gather(const S *__restrict__ fin, KParams p, int c0, int c1, d
     double sum = 0, jx = 0, jy = 0, jz = 0;
     for (int i = 0; i < NQ; i++) {
         size_t idx;
-        if (i == 0) idx = c;
-        else if (fl & (1u << i)) idx = (size_t)opp(i) * N + c;
-        else idx = (size_t)i * N + (size_t)(p.rows[r].nb[nbk(i)] + x - cx(i));
+        if (i == 0) idx = pidx(0, (uint32_t)c, (uint32_t)N);
+        else if (fl & (1u << i)) idx = pidx(opp(i), (uint32_t)c, (uint32_t)N);
+        else idx = pidx(i, (uint32_t)(p.rows[r].nb[nbk(i)] + x - cx(i)), (uint32_t)N);
         const double fi = (double)Storage<S>::ld(fin + idx) + wgt(i);
         if (fout19) fout19[i * M + k] = fi;
         sum += fi;
@@ -220,9 +220,9 @@ __global__ void k_init(S *__restrict__ fout, KParams p, const double *__restrict
     for (int i = 0; i < NQ; i++) {
         const double s = f19[i * M + (c - c0)] - wgt(i);
         size_t idx;
-        if (i == 0) idx = c;
-        else if (fl & (1u << i)) idx = (size_t)opp(i) * N + c;
-        else idx = (size_t)i * N + (size_t)(p.rows[r].nb[nbk(i)] + x - cx(i));
+        if (i == 0) idx = pidx(0, (uint32_t)c, (uint32_t)N);
+        else if (fl & (1u << i)) idx = pidx(opp(i), (uint32_t)c, (uint32_t)N);
+        else idx = pidx(i, (uint32_t)(p.rows[r].nb[nbk(i)] + x - cx(i)), (uint32_t)N);
         Storage<S>::st(fout + idx, (typename Storage<S>::R)s);
     }
 }
@@ -246,9 +246,9 @@ __global__ void k_wall_shear(const S *__restrict__ fin, KParams p, int c0, int c
     double f[NQ], sum = 0, jx = 0, jy = 0, jz = 0, n[3] = {0, 0, 0};
     for (int i = 0; i < NQ; i++) {
         size_t idx;
-        if (i == 0) idx = c;
-        else if (fl & (1u << i)) idx = (size_t)opp(i) * N + c;
-        else idx = (size_t)i * N + (size_t)(p.rows[r].nb[nbk(i)] + x - cx(i));
+        if (i == 0) idx = pidx(0, (uint32_t)c, (uint32_t)N);
+        else if (fl & (1u << i)) idx = pidx(opp(i), (uint32_t)c, (uint32_t)N);
+        else idx = pidx(i, (uint32_t)(p.rows[r].nb[nbk(i)] + x - cx(i)), (uint32_t)N);
         f[i] = (double)Storage<S>::ld(fin + idx) + wgt(i);
         sum += f[i];
         jx += cx(i) * f[i];
@@ -311,9 +311,9 @@ __global__ void k_init_eq(S *__restrict__ fout, KParams p, const double *__restr
         const double eu = cx(i) * vx + cy(i) * vy + cz(i) * vz;
         const double s = wgt(i) * (3.0 * P - 1.0 + 3.0 * eu + 4.5 * eu * eu - usq);  // f^eq_i - w_i
         size_t idx;
-        if (i == 0) idx = c;
-        else if (fl & (1u << i)) idx = (size_t)opp(i) * N + c;
-        else idx = (size_t)i * N + (size_t)(p.rows[r].nb[nbk(i)] + x - cx(i));
+        if (i == 0) idx = pidx(0, (uint32_t)c, (uint32_t)N);
+        else if (fl & (1u << i)) idx = pidx(opp(i), (uint32_t)c, (uint32_t)N);
+        else idx = pidx(i, (uint32_t)(p.rows[r].nb[nbk(i)] + x - cx(i)), (uint32_t)N);
         Storage<S>::st(fout + idx, (typename Storage<S>::R)s);
     }
 }

@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(256, MINB)
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
     if (t == 0 && p.step) *p.step += 1;  // the step index t_n seen by the boundary kernels
-    // population i of cell k lives at fin[i * N + k]; 19 N < 2^31 is checked at creation
+    // population i of cell k lives at fin[pidx(i, k, N)]; 19 N < 2^31 is checked at creation
     const uint32_t N = (uint32_t)p.n;
     R f[CPT][NQ];
     R om[CPT];
@@ -44,9 +44,9 @@ __global__ void __launch_bounds__(256, MINB)
 #pragma unroll
         for (int i = 0; i < NQ; i++) {
             uint32_t off;
-            if (i == 0) off = (uint32_t)c;
-            else if (fl[u] & (1u << i)) off = (uint32_t)opp(i) * N + (uint32_t)c;
-            else off = (uint32_t)i * N + (uint32_t)(__ldg(&nb[nbk(i)]) + x - cx(i));
+            if (i == 0) off = pidx(0, (uint32_t)c, N);
+            else if (fl[u] & (1u << i)) off = pidx(opp(i), (uint32_t)c, N);
+            else off = pidx(i, (uint32_t)(__ldg(&nb[nbk(i)]) + x - cx(i)), N);
             f[u][i] = Storage<S>::ld(fin + off);
         }
     }
@@ -95,7 +95,7 @@ __global__ void __launch_bounds__(256, MINB)
                 const R vb = vx * bx + vy * by + vz * bz;
                 post += kf * w * (R(3) * (eb - vb) + R(9) * eu * eb);
             }
-            Storage<S>::st(fout + ((uint32_t)i * N + (uint32_t)c), post);
+            Storage<S>::st(fout + pidx(i, (uint32_t)c, N), post);
         }
     }
 }

@@ -2,7 +2,6 @@
 no GPU): the compact row layout of the workloads passes its built-in
 self-check (every population pull resolves to its own stored cell), the
 sizes match the inputs, and invalid inputs are rejected with a reason."""
-import numpy as np
 import pytest
 
 from workloads import aorta, configs

@@ -14,7 +14,6 @@ axisymmetric pipe flow.
   tube.
 """
 import numpy as np
-import pytest
 from scipy import special
 
 import oracle.axisym as ax

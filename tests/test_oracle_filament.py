@@ -12,7 +12,6 @@
   the central-difference scheme predicts.
 """
 import numpy as np
-import pytest
 
 import oracle
 from workloads import IBNodes, Instance, geometry

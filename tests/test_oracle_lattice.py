@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from workloads import BC_PRESSURE, BC_RCR, BC_VELOCITY, Boundary, Instance, configs, geometry, profiles
+from workloads import BC_RCR, BC_VELOCITY, Boundary, Instance, configs, geometry, profiles
 
 CS2 = 1.0 / 3.0
 TAU_MAGIC = 0.5 + np.sqrt(3.0 / 16.0)
