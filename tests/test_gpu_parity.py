@@ -264,3 +264,28 @@ def test_fields_device_matches_host(Lattice):
     host = lat.fields(0)
     for t, h in zip(outs, host):
         assert np.array_equal(t.cpu().numpy(), h.astype(np.float32))
+
+
+def test_degenerate_instances(Lattice):
+    # an instance without fluid, a single fluid cell and an ordinary tube in
+    # one batch: the empty and single-cell ones stay at rest, the tube runs
+    # exactly as it does alone
+    empty = Instance(node=np.ones((4, 5, 6), np.uint8), tau=0.8)
+    one = np.ones((3, 3, 3), np.uint8)
+    one[1, 1, 1] = 0
+    single = Instance(node=one, tau=0.7)
+    tube = configs.lv_tube(period=300)
+    lat = Lattice([empty, single, tube], precision="f64")
+    lat.step(150)
+    lat.sync()
+    alone = Lattice([tube], precision="f64")
+    alone.step(150)
+    assert np.array_equal(lat.populations(2), alone.populations(0))
+    assert np.array_equal(lat.waves(2), alone.waves(0))
+    assert np.abs(lat.populations(0)).max() == 0.0
+    P, jx, jy, jz = lat.fields(1)
+    assert P[13] == pytest.approx(1 / 3, abs=1e-15) and max(abs(jx[13]), abs(jy[13]), abs(jz[13])) < 1e-16
+    only_empty = Lattice([empty], precision="f32")
+    only_empty.step(10)
+    only_empty.sync()
+    assert np.abs(only_empty.fields(0)[0]).max() == 0.0
