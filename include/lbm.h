@@ -260,6 +260,11 @@ lbm_status lbm_cycle_change(lbm_handle *h, const int64_t *period, double *delta)
  * and keeps the fastest.  Returns the chosen block size, minimum blocks and
  * cells per thread; times_ms (NULL or 20 doubles, variant-major) receives the
  * mean launch time of every candidate. */
+/* Sets the stream-collide launch shape directly: block size (multiple of 32
+ * in [32, 256]) and variant 0..4 in the order of lbm_autotune's list (for
+ * reproducible timings and tests); LBM_ERR_ARG otherwise. */
+lbm_status lbm_set_stream_collide_shape(lbm_handle *h, int block, int variant);
+
 lbm_status lbm_autotune(lbm_handle *h, int iters, int *block, int *min_blocks, int *cells_per_thread,
                         double *times_ms);
 

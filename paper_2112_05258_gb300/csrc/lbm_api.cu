@@ -897,6 +897,17 @@ lbm_status lbm_cycle_change(lbm_handle *h, const int64_t *period, double *delta)
     return LBM_OK;
 }
 
+lbm_status lbm_set_stream_collide_shape(lbm_handle *h, int block, int variant) {
+    if (!h || block < 32 || block > 256 || (block % 32) != 0 || variant < 0 || variant >= SC_VARIANTS)
+        return fail(h, LBM_ERR_ARG, "block must be a multiple of 32 in [32, 256], variant in [0, 4]");
+    CK(h, cudaSetDevice(h->device));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (block != h->block || variant != h->variant) drop_graphs(h);
+    h->block = block;
+    h->variant = variant;
+    return LBM_OK;
+}
+
 lbm_status lbm_autotune(lbm_handle *h, int iters, int *block, int *min_blocks, int *cells_per_thread,
                         double *times_ms) {
     if (!h || iters < 1 || !block || !min_blocks || !cells_per_thread) return fail(h, LBM_ERR_ARG, "bad arguments");

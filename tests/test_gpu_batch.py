@@ -102,3 +102,23 @@ def test_uneven_batch_equals_single(Lattice):
         single.step(300)
         assert np.array_equal(lat.populations(q), single.populations(0))
         assert np.array_equal(lat.waves(q), single.waves(0))
+
+
+@pytest.mark.parametrize("variant", range(5))
+def test_every_stream_collide_variant_gives_the_trajectory(Lattice, variant):
+    # the occupancy and cells-per-thread variants run the same per-cell arithmetic
+    insts = [configs.lv_tube(period=300), configs.ib_tube()]
+    ref = Lattice(insts, precision="f64")
+    ref.step(120)
+    lat = Lattice(insts, precision="f64")
+    lat.set_stream_collide_shape(96 if variant % 2 else 128, variant)
+    lat.step(120)
+    for q in range(2):
+        assert np.abs(lat.populations(q) - ref.populations(q)).max() < 1e-14
+        assert np.abs(lat.waves(q)[:, 1:] - ref.waves(q)[:, 1:]).max() < 1e-14
+    f32 = Lattice(insts, precision="f16")
+    f32.set_stream_collide_shape(128, variant)
+    f32.step(60)
+    g32 = Lattice(insts, precision="f16")
+    g32.step(60)
+    assert np.abs(f32.populations(0) - g32.populations(0)).max() < 1e-6
