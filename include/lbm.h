@@ -165,7 +165,10 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out);
 
 /* Replaces the params of boundary bc of instance inst (same layout as in
  * lbm_boundary_desc; for LV/RCR the state entries P_v0 / P_w0 are ignored
- * after creation).  Enqueued in stream order. */
+ * after creation).  Enqueued in stream order without waiting for the
+ * stream: p is copied at the call into a pinned staging ring of the handle
+ * (64 slots; a call waits only for the copy that last used its slot), and
+ * steps enqueued after the call use the new params. */
 lbm_status lbm_set_0d_params(lbm_handle *h, int inst, int bc, const double *p, int np);
 
 /* Sets f_i(x, t_0) of every fluid node of instance inst from a host array of
@@ -198,6 +201,14 @@ lbm_status lbm_read_populations(lbm_handle *h, int inst, double *f);
 /* 8 doubles: {t_{n+1}, Q(t_n), Q_u(t_n), Pbar_gauge(t_n), state (P_w, P_v
  * or P*-P_ref), C_v(t_{n+1}) P_v (LV) or 0, valve_open, T_d}. */
 lbm_status lbm_read_0d_state(lbm_handle *h, int inst, int bc, double *out);
+
+/* The same 8 doubles for every boundary of instance inst (boundary-major,
+ * 8 * n_bc doubles), enqueued on the handle's stream without waiting: the
+ * values are those after the steps enqueued before the call, and `out` is
+ * filled when the stream reaches the call (lbm_sync, or an event on the
+ * stream).  `out` must be page-locked host memory (cudaHostAlloc, or a
+ * pinned torch tensor) that stays valid until then. */
+lbm_status lbm_read_0d_state_async(lbm_handle *h, int inst, double *out);
 
 /* The last min(steps, capacity, max_rows) steps of instance inst: rows of
  * 1 + 4*n_bc doubles {step, then per boundary Q_u, Pbar_gauge, state,

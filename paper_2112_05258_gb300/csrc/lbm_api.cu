@@ -59,6 +59,12 @@ struct lbm_handle {
     uint64_t *ibmask = nullptr;
     double *rd_f19 = nullptr, *rd_mac = nullptr;  // read-out scratch, largest instance (allocated on first use)
     int32_t *cell_box_dev = nullptr;               // box index of every stored cell (allocated on first use)
+    // stream-ordered 0D parameter updates: pinned staging ring, one event per slot
+    static constexpr int PAR_RING = 64;
+    BcParam *par_ring = nullptr;
+    cudaEvent_t par_ev[PAR_RING] = {};
+    int par_pos = 0;
+    double *state_rows = nullptr;                  // 8 per boundary, for the asynchronous read
     int64_t max_inst_cells = 0;
     int variant = 0;  // stream-collide occupancy variant (see launch_stream_collide)
     int *inst_bc = nullptr;  // per instance: bc_first, n_bc
@@ -500,8 +506,30 @@ lbm_status lbm_set_0d_params(lbm_handle *h, int inst, int bc, const double *p, i
         return fail(h, LBM_ERR_ARG, "0D scheme order must be 0, 1, 2 or 4");
     for (int k = 0; k < np; k++) bp.par[k] = p[k];
     CK(h, cudaSetDevice(h->device));
-    CK(h, cudaStreamSynchronize(h->stream));
-    CK(h, cudaMemcpy(&h->bc_par[ip.bc_first + bc], &bp, sizeof(BcParam), cudaMemcpyHostToDevice));
+    if (!h->par_ring) {
+        CK(h, cudaHostAlloc((void **)&h->par_ring, lbm_handle::PAR_RING * sizeof(BcParam), cudaHostAllocDefault));
+        for (int k = 0; k < lbm_handle::PAR_RING; k++)
+            CK(h, cudaEventCreateWithFlags(&h->par_ev[k], cudaEventDisableTiming));
+    }
+    const int slot = h->par_pos++ % lbm_handle::PAR_RING;
+    CK(h, cudaEventSynchronize(h->par_ev[slot]));  // the copy that last used this slot has run
+    h->par_ring[slot] = bp;
+    CK(h, cudaMemcpyAsync(&h->bc_par[ip.bc_first + bc], &h->par_ring[slot], sizeof(BcParam),
+                          cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaEventRecord(h->par_ev[slot], h->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_read_0d_state_async(lbm_handle *h, int inst, double *out) {
+    if (bad_inst(h, inst) || !out) return fail(h, LBM_ERR_ARG, "bad instance or array");
+    const InstParam &ip = h->L.inst[inst];
+    if (ip.n_bc == 0) return LBM_OK;
+    CK(h, cudaSetDevice(h->device));
+    if (!h->state_rows) CK(h, dalloc(h, &h->state_rows, 8 * std::max<size_t>(1, h->L.bc.size())));
+    double *rows = h->state_rows + 8 * (size_t)ip.bc_first;
+    CK(h, launch_state_rows(h->bc_state, h->bc_par, h->etab, ip.bc_first, ip.n_bc, (int)h->L.bc.size(),
+                            (long long)h->steps, rows, h->stream));
+    CK(h, cudaMemcpyAsync(out, rows, 8 * (size_t)ip.n_bc * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     return LBM_OK;
 }
 
@@ -976,6 +1004,10 @@ void lbm_destroy(lbm_handle *h) {
     for (int k = 0; k < 2; k++)
         if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
     for (auto e : h->ev) cudaEventDestroy(e);
+    if (h->par_ring) {
+        for (auto e : h->par_ev) cudaEventDestroy(e);
+        cudaFreeHost(h->par_ring);
+    }
     for (void *p : h->allocs) cudaFree(p);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;

@@ -378,6 +378,34 @@ cudaError_t launch_gather(int prec, const void *fin, const KParams &p, int c0, i
     return cudaGetLastError();
 }
 
+// 0D state rows of boundaries [b0, b0 + nb) for lbm_read_0d_state_async:
+// {t, Q, Q_u, Pbar_gauge, state, C_v P_v (LV), valve_open, T_d}
+__global__ void k_state_rows(const BcState *__restrict__ st, const BcParam *__restrict__ par,
+                             const double *__restrict__ etab, int b0, int nb, int nbc_total, long long steps,
+                             double *out8) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    const int b = b0 + k;
+    const BcState s = st[(size_t)(steps & 1) * nbc_total + b];
+    const BcParam &P = par[b];
+    double *o = out8 + 8 * (size_t)k;
+    o[0] = (double)steps;
+    o[1] = s.Q;
+    o[2] = s.Qu;
+    o[3] = s.Pbar - 1.0 / 3.0;
+    o[4] = P.kind == BC_RCR ? s.Pw : (P.kind == BC_LV ? s.Pv : s.Pstar_gauge);
+    o[5] = P.kind == BC_LV ? s.Pv / etab[2 * (P.etab_off + (int)(steps % P.period))] : 0.0;
+    o[6] = s.valve_open;
+    o[7] = s.Td;
+}
+
+cudaError_t launch_state_rows(const BcState *st, const BcParam *par, const double *etab, int b0, int nb,
+                              int nbc_total, long long steps, double *out8, cudaStream_t s) {
+    if (nb == 0) return cudaSuccess;
+    k_state_rows<<<1, 32 * ((nb + 31) / 32), 0, s>>>(st, par, etab, b0, nb, nbc_total, steps, out8);
+    return cudaGetLastError();
+}
+
 // compact -> box scatter of the gathered P, j into FP32 device arrays
 __global__ void k_scatter_box(const double *__restrict__ mac4, int M, const int32_t *__restrict__ box, float *P,
                               float *jx, float *jy, float *jz) {

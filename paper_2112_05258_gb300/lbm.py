@@ -71,7 +71,8 @@ EXPORTS = ["lbm_create", "lbm_set_0d_params", "lbm_init_populations", "lbm_step"
            "lbm_get_info", "lbm_last_error", "lbm_destroy", "lbm_boundary_flux_noalloc",
            "lbm_init_equilibrium", "lbm_set_0d_state", "lbm_cycle_change", "lbm_autotune",
            "lbm_wall_shear", "lbm_check_config", "lbm_checkpoint_size", "lbm_checkpoint_save",
-           "lbm_checkpoint_load", "lbm_read_fields_device", "lbm_set_stream_collide_shape"]
+           "lbm_checkpoint_load", "lbm_read_fields_device", "lbm_set_stream_collide_shape",
+           "lbm_read_0d_state_async"]
 
 _lib = None
 
@@ -109,6 +110,7 @@ def load(path: Optional[str] = None):
     L.lbm_wall_shear.argtypes = [H, ctypes.c_int, _dp]
     L.lbm_checkpoint_size.argtypes = [H, ctypes.POINTER(ctypes.c_int64)]
     L.lbm_set_stream_collide_shape.argtypes = [H, ctypes.c_int, ctypes.c_int]
+    L.lbm_read_0d_state_async.argtypes = [H, ctypes.c_int, ctypes.c_void_p]
     L.lbm_read_fields_device.argtypes = [H, ctypes.c_int] + [ctypes.c_void_p] * 4
     L.lbm_checkpoint_save.argtypes = [H, ctypes.c_void_p, ctypes.c_int64]
     L.lbm_checkpoint_load.argtypes = [H, ctypes.c_void_p, ctypes.c_int64]
@@ -367,6 +369,12 @@ class Lattice:
         out = np.empty(self.n_instances)
         self._ck(load().lbm_cycle_change(self._h, per.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _p(out)))
         return out
+
+    def state_0d_async(self, inst: int, out_ptr: int):
+        """Enqueues the 8-value 0D state rows of every boundary of instance
+        inst into page-locked host memory at out_ptr (8 * n_bc doubles),
+        filled when the lattice's stream reaches the call."""
+        self._ck(load().lbm_read_0d_state_async(self._h, inst, ctypes.c_void_p(int(out_ptr))))
 
     def set_stream_collide_shape(self, block: int, variant: int):
         """Fixes the stream-collide block size and variant (0..4)."""

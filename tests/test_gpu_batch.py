@@ -122,3 +122,49 @@ def test_every_stream_collide_variant_gives_the_trajectory(Lattice, variant):
     g32 = Lattice(insts, precision="f16")
     g32.step(60)
     assert np.abs(f32.populations(0) - g32.populations(0)).max() < 1e-6
+
+
+def test_set_0d_params_is_stream_ordered(Lattice):
+    # parameters set before the first step equal a lattice created with them
+    # (and the oracle); set between queued steps they act from the next step
+    # on, with or without the host waiting in between
+    import oracle
+    inst = configs.rigid_tube(16, 16, 24, radius=5.0, period=200)
+    new = [0.05, 120.0, 0.7, 0.0]
+    inst2 = configs.rigid_tube(16, 16, 24, radius=5.0, period=200, rcr=tuple(new))
+    a = Lattice([inst], precision="f64")
+    a.set_0d_params(0, 1, new)
+    a.step(150)
+    o = oracle.Oracle(inst2)
+    o.step(150)
+    assert np.abs(a.waves(0)[:, 1:] - o.waves()[:, 1:]).max() < 1e-12
+    queued = Lattice([inst], precision="f32", graph_steps=16)
+    queued.step(100)
+    queued.set_0d_params(0, 1, new)          # no wait for the 100 steps
+    queued.step(100)
+    waited = Lattice([inst], precision="f32", graph_steps=16)
+    waited.step(100)
+    waited.sync()
+    waited.set_0d_params(0, 1, new)
+    waited.step(100)
+    plain = Lattice([inst], precision="f32", graph_steps=16)
+    plain.step(200)
+    wq, ww, wp = queued.waves(0), waited.waves(0), plain.waves(0)
+    assert np.array_equal(wq, ww)
+    assert np.array_equal(wq[:100], wp[:100]) and not np.array_equal(wq[100:], wp[100:])
+
+
+def test_async_0d_state_read_equals_sync(Lattice):
+    torch = pytest.importorskip("torch")
+    insts = [configs.lv_tube(period=300), configs.rigid_tube(16, 16, 24, radius=5.0, period=200)]
+    lat = Lattice(insts, precision="f32")
+    bufs = [torch.zeros(8 * 2, dtype=torch.float64, pin_memory=True) for _ in range(3)]
+    for k in range(3):
+        lat.step(37)
+        lat.state_0d_async(k % 2, bufs[k].data_ptr())
+    lat.sync()
+    # the last read is of instance 0 after 111 steps
+    got = bufs[2].numpy().reshape(2, 8)
+    for bc in range(2):
+        assert np.array_equal(got[bc], lat.state_0d(0, bc))
+    assert bufs[0].numpy()[0] == 37.0 and bufs[1].numpy()[0] == 74.0
