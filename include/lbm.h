@@ -177,7 +177,8 @@ lbm_status lbm_set_0d_params(lbm_handle *h, int inst, int bc, const double *p, i
 lbm_status lbm_init_populations(lbm_handle *h, int inst, const double *f);
 
 /* Advances all instances by n steps (Algorithm 1).  Asynchronous: returns
- * after enqueueing (as CUDA graphs of graph_steps steps where possible). */
+ * after enqueueing, as CUDA graphs of graph_steps steps and, for the
+ * remainder, single-step graphs (each captured once per step parity). */
 lbm_status lbm_step(lbm_handle *h, int64_t n);
 
 /* Waits for the stream; returns LBM_ERR_UNSTABLE if the device status word

@@ -77,6 +77,7 @@ struct lbm_handle {
     IbKParams ibp{};
     int64_t steps = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph1[2] = {nullptr, nullptr};  // single steps (by parity), for step counts below graph_steps
     // kernel timing
     bool timing = false;
     std::vector<cudaEvent_t> ev;
@@ -248,6 +249,26 @@ lbm_status ensure_graph(lbm_handle *h) {
     return LBM_OK;
 }
 
+// one step as a graph (one launch instead of five for single-step callers)
+lbm_status ensure_graph1(lbm_handle *h) {
+    const int par = h->parity;
+    if (h->graph1[par]) return LBM_OK;
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    lbm_status st = launch_step(h, false);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    h->parity = par;  // capture does not run anything
+    if (st != LBM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    CK(h, e);
+    e = cudaGraphInstantiate(&h->graph1[par], g, 0);
+    cudaGraphDestroy(g);
+    CK(h, e);
+    return LBM_OK;
+}
+
 lbm_status read_gather(lbm_handle *h, int inst, bool with_f) {
     const size_t m = (size_t)h->max_inst_cells;
     if (with_f && !h->rd_f19) CK(h, dalloc(h, &h->rd_f19, 19 * m));
@@ -260,11 +281,16 @@ lbm_status read_gather(lbm_handle *h, int inst, bool with_f) {
 }
 
 void drop_graphs(lbm_handle *h) {
-    for (int k = 0; k < 2; k++)
+    for (int k = 0; k < 2; k++) {
         if (h->graph[k]) {
             cudaGraphExecDestroy(h->graph[k]);
             h->graph[k] = nullptr;
         }
+        if (h->graph1[k]) {
+            cudaGraphExecDestroy(h->graph1[k]);
+            h->graph1[k] = nullptr;
+        }
+    }
 }
 
 bool bad_inst(lbm_handle *h, int inst) { return !h || inst < 0 || inst >= (int)h->inst.size(); }
@@ -575,8 +601,10 @@ lbm_status lbm_step(lbm_handle *h, int64_t n) {
         h->steps += h->graph_steps;
     }
     for (; left > 0; left--) {
-        lbm_status s = launch_step(h, false);
+        lbm_status s = ensure_graph1(h);
         if (s != LBM_OK) return s;
+        CK(h, cudaGraphLaunch(h->graph1[h->parity], h->stream));
+        h->parity = 1 - h->parity;
         h->steps++;
     }
     return LBM_OK;
@@ -1001,8 +1029,10 @@ void lbm_destroy(lbm_handle *h) {
     if (!h) return;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
-    for (int k = 0; k < 2; k++)
+    for (int k = 0; k < 2; k++) {
         if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
+        if (h->graph1[k]) cudaGraphExecDestroy(h->graph1[k]);
+    }
     for (auto e : h->ev) cudaEventDestroy(e);
     if (h->par_ring) {
         for (auto e : h->par_ev) cudaEventDestroy(e);
