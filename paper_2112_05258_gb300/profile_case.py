@@ -52,7 +52,7 @@ def main():
     else:
         inst = aorta.build(0)
     lat = Lattice([inst], precision=args.precision, block_size=args.block,
-                  graph_steps=2 * (args.steps + 1))  # graphs longer than the run: direct launches only
+                  graph_steps=2 * (args.steps + 1))  # graphs longer than the run: single-step graphs only
     info = lat.info()
     t0 = time.perf_counter()
     lat.step(args.steps)
