@@ -219,7 +219,11 @@ lbm_status launch_step(lbm_handle *h, bool timed) {
         e1 = h->ev[h->ev_used++];
         CK(h, cudaEventRecord(e0, h->stream));
     }
-    CK(h, launch_stream_collide(h->prec, fin, fout, h->kp, h->block, h->variant, h->stream));
+    // without wall nodes, every other step runs in descending cell order and
+    // starts on the lines the step before finished on (the band-velocity
+    // kernel takes that role when there are wall nodes)
+    const int desc = h->ibp.n_nodes ? 0 : h->parity;
+    CK(h, launch_stream_collide(h->prec, fin, fout, h->kp, h->block, h->variant, h->stream, desc));
     if (timed) {
         CK(h, cudaEventRecord(e1, h->stream));
         h->timed_launches++;

@@ -18,11 +18,13 @@
 
 namespace lbm {
 
+// Blocks take the band in descending cell order: stream-collide finished on
+// the highest cells, whose lines are still in L2.
 template <class S>
 __global__ void k_band_moments(const S *__restrict__ fin, KParams p, IbKParams ib) {
     using R = typename Storage<S>::R;
     using V = typename Vec4<R>::T;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = (int)(gridDim.x - 1 - blockIdx.x) * blockDim.x + threadIdx.x;
     if (t >= ib.n_band) return;
     const int c = ib.band[t];
     const uint32_t fl = p.flags[c];

@@ -79,7 +79,7 @@ constexpr int SC_VARIANTS = 5;
 int stream_collide_min_blocks(int variant);
 int stream_collide_cells_per_thread(int variant);
 cudaError_t launch_stream_collide(int prec, const void *fin, void *fout, const KParams &p, int block,
-                                  int variant, cudaStream_t s);
+                                  int variant, cudaStream_t s, int desc = 0);
 cudaError_t launch_boundary(int prec, void *f, const KParams &p, const BcKParams &q, cudaStream_t s);
 cudaError_t launch_gather(int prec, const void *fin, const KParams &p, int c0, int c1, double *f19, double *mac4,
                           cudaStream_t s);

@@ -18,12 +18,15 @@ namespace lbm {
 // with spills).  CPT > 1 gives each thread CPT independent cells, one grid
 // stride apart, whose loads are all issued before any of them is consumed
 // (more bytes in flight per thread at a lower occupancy).  The variants are
-// kept for the run-time autotuner.
+// kept for the run-time autotuner.  desc = 1 maps the blocks to the cells in
+// descending order, so that a launch starts on the lines the previous kernel
+// touched last (still in L2).
 template <class S, int MINB, int CPT>
 __global__ void __launch_bounds__(256, MINB)
-    k_stream_collide(const S *__restrict__ fin, S *__restrict__ fout, KParams p) {
+    k_stream_collide(const S *__restrict__ fin, S *__restrict__ fout, KParams p, int desc) {
     using R = typename Storage<S>::R;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int bid = desc ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+    const int t = bid * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
     if (t == 0 && p.step) *p.step += 1;  // the step index t_n seen by the boundary kernels
     // population i of cell k lives at fin[pidx(i, k, N)]; 19 N < 2^31 is checked at creation
@@ -110,25 +113,25 @@ int stream_collide_min_blocks(int variant) { return kVariants[variant][0]; }
 int stream_collide_cells_per_thread(int variant) { return kVariants[variant][1]; }
 
 cudaError_t launch_stream_collide(int prec, const void *fin, void *fout, const KParams &p, int block,
-                                  int variant, cudaStream_t s) {
+                                  int variant, cudaStream_t s, int desc) {
     if (p.n == 0) return cudaSuccess;
     const int cpt = kVariants[variant][1];
     const int grid = (int)((p.n + (long long)block * cpt - 1) / ((long long)block * cpt));
     switch (variant) {
     case 1:
-        DISPATCH(prec, (k_stream_collide<S, 8, 1><<<grid, block, 0, s>>>(static_cast<const S *>(fin), as<S>(fout), p)));
+        DISPATCH(prec, (k_stream_collide<S, 8, 1><<<grid, block, 0, s>>>(static_cast<const S *>(fin), as<S>(fout), p, desc)));
         break;
     case 2:
-        DISPATCH(prec, (k_stream_collide<S, 5, 1><<<grid, block, 0, s>>>(static_cast<const S *>(fin), as<S>(fout), p)));
+        DISPATCH(prec, (k_stream_collide<S, 5, 1><<<grid, block, 0, s>>>(static_cast<const S *>(fin), as<S>(fout), p, desc)));
         break;
     case 3:
-        DISPATCH(prec, (k_stream_collide<S, 4, 2><<<grid, block, 0, s>>>(static_cast<const S *>(fin), as<S>(fout), p)));
+        DISPATCH(prec, (k_stream_collide<S, 4, 2><<<grid, block, 0, s>>>(static_cast<const S *>(fin), as<S>(fout), p, desc)));
         break;
     case 4:
-        DISPATCH(prec, (k_stream_collide<S, 3, 2><<<grid, block, 0, s>>>(static_cast<const S *>(fin), as<S>(fout), p)));
+        DISPATCH(prec, (k_stream_collide<S, 3, 2><<<grid, block, 0, s>>>(static_cast<const S *>(fin), as<S>(fout), p, desc)));
         break;
     default:
-        DISPATCH(prec, (k_stream_collide<S, 6, 1><<<grid, block, 0, s>>>(static_cast<const S *>(fin), as<S>(fout), p)));
+        DISPATCH(prec, (k_stream_collide<S, 6, 1><<<grid, block, 0, s>>>(static_cast<const S *>(fin), as<S>(fout), p, desc)));
         break;
     }
     return cudaGetLastError();
