@@ -444,7 +444,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
              ck(upload(h, &h->fil_count, L.fil_count), "filaments") &&
              ck(upload(h, &h->fil_par, L.fil_par), "filaments") &&
              (L.fil_start.empty() || ck(prepare_filament_kernel(L.max_fil), "filament kernel")) &&
-             ck(dalloc_bytes(h, &h->vband, 4 * n * h->rbytes), "vband");
+             ck(dalloc_bytes(h, &h->vband, 4 * n * h->rbytes), "vband") &&
+             ck(cudaMemset(h->vband, 0, 4 * n * h->rbytes), "vband");
     }
     {
         std::vector<int> ib2;  // bc_first of every instance, then n_bc of every instance

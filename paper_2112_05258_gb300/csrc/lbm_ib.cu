@@ -140,10 +140,13 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib) {
                 for (int dx = 0; dx < 4; dx++) {
                     const int bit = d[0] + dx + 1 + 6 * (jy + 6 * jz);
                     const uint64_t word = bit < 64 ? m0 : bit < 128 ? m1 : bit < 192 ? m2 : m3;
-                    if (!((word >> (bit & 63)) & 1ull)) continue;  // wall or boundary slot: no fluid
-                    valid |= 1ull << (dx + 4 * (dy + 4 * j));
-                    const V v = vb[base + i0[0] + dx - 1];
-                    const R dd = w[0][dx] * wyz;
+                    const bool ok = (word >> (bit & 63)) & 1ull;  // else a wall or boundary slot: no fluid
+                    valid |= (uint64_t)ok << (dx + 4 * (dy + 4 * j));
+                    // branch-free, so that the loads can all be in flight: a
+                    // missing cell reads slot 0 (zeroed at creation, finite)
+                    // with weight 0
+                    const V v = vb[ok ? base + i0[0] + dx - 1 : 0];
+                    const R dd = ok ? w[0][dx] * wyz : R(0);
                     vx += v.x * dd;
                     vy += v.y * dd;
                     vz += v.z * dd;
@@ -152,8 +155,8 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib) {
         }
     }
     if (out_of_band) atomicOr(p.status, 2u);
+    const unsigned grp = TPN > 1 ? ((1u << TPN) - 1u) << ((threadIdx.x & 31) & ~(TPN - 1)) : 0u;
     if (TPN > 1) {
-        const unsigned grp = ((1u << TPN) - 1u) << ((threadIdx.x & 31) & ~(TPN - 1));
 #pragma unroll
         for (int o = 1; o < TPN; o <<= 1) {
             vx += __shfl_xor_sync(grp, vx, o, TPN);
@@ -161,22 +164,32 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib) {
             vz += __shfl_xor_sync(grp, vz, o, TPN);
         }
     }
-    const double Vf[3] = {(double)vx, (double)vy, (double)vz};
+    // the penalty force (FP64) on lane 0 of the node's group, which then
+    // hands F dA to the other lanes for their planes of the spreading
     double F[3], Vs[3];
+    R Fx = 0, Fy = 0, Fz = 0;
+    if (q == 0) {
+        const double Vf[3] = {(double)vx, (double)vy, (double)vz};
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-        Vs[a] = ib.Vs[3 * s + a];
-        const double dv = Vf[a] - Vs[a];
-        const double I = ib.I[3 * s + a] + dv;
-        F[a] = ip.alpha * I + ip.beta * dv;
-        if (q == 0) {
+        for (int a = 0; a < 3; a++) {
+            Vs[a] = ib.Vs[3 * s + a];
+            const double dv = Vf[a] - Vs[a];
+            const double I = ib.I[3 * s + a] + dv;
+            F[a] = ip.alpha * I + ip.beta * dv;
             ib.I[3 * s + a] = I;
             ib.F[3 * s + a] = F[a];
             ib.Vf[3 * s + a] = Vf[a];
         }
+        const R dA = (R)ib.dA[s];
+        Fx = (R)F[0] * dA;
+        Fy = (R)F[1] * dA;
+        Fz = (R)F[2] * dA;
     }
-    const R dA = (R)ib.dA[s];
-    const R Fx = (R)F[0] * dA, Fy = (R)F[1] * dA, Fz = (R)F[2] * dA;
+    if (TPN > 1) {
+        Fx = __shfl_sync(grp, Fx, 0, TPN);
+        Fy = __shfl_sync(grp, Fy, 0, TPN);
+        Fz = __shfl_sync(grp, Fz, 0, TPN);
+    }
     V *b = static_cast<V *>(const_cast<void *>(p.b));
 #pragma unroll
     for (int k = 0; k < 16 * PL; k++) {
