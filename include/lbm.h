@@ -166,9 +166,10 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out);
 /* Replaces the params of boundary bc of instance inst (same layout as in
  * lbm_boundary_desc; for LV/RCR the state entries P_v0 / P_w0 are ignored
  * after creation).  Enqueued in stream order without waiting for the
- * stream: p is copied at the call into a pinned staging ring of the handle
- * (64 slots; a call waits only for the copy that last used its slot), and
- * steps enqueued after the call use the new params. */
+ * stream: p is copied at the call into a mapped page-locked staging ring of
+ * the handle (64 slots; a call waits only for the transfer that last used its
+ * slot), a one-warp kernel moves it to the device, and steps enqueued after
+ * the call use the new params. */
 lbm_status lbm_set_0d_params(lbm_handle *h, int inst, int bc, const double *p, int np);
 
 /* Sets f_i(x, t_0) of every fluid node of instance inst from a host array of
@@ -208,7 +209,9 @@ lbm_status lbm_read_0d_state(lbm_handle *h, int inst, int bc, double *out);
  * values are those after the steps enqueued before the call, and `out` is
  * filled when the stream reaches the call (lbm_sync, or an event on the
  * stream).  `out` must be page-locked host memory (cudaHostAlloc, or a
- * pinned torch tensor) that stays valid until then. */
+ * pinned torch tensor) that stays valid until then; where the device can
+ * address it (unified addressing), the kernel that forms the rows writes
+ * them there directly, else they go through a device buffer and a copy. */
 lbm_status lbm_read_0d_state_async(lbm_handle *h, int inst, double *out);
 
 /* The last min(steps, capacity, max_rows) steps of instance inst: rows of

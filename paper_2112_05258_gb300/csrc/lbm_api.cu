@@ -61,7 +61,7 @@ struct lbm_handle {
     int32_t *cell_box_dev = nullptr;               // box index of every stored cell (allocated on first use)
     // stream-ordered 0D parameter updates: pinned staging ring, one event per slot
     static constexpr int PAR_RING = 64;
-    BcParam *par_ring = nullptr;
+    BcParam *par_ring = nullptr, *par_ring_dev = nullptr;  // host and device addresses of the mapped ring
     cudaEvent_t par_ev[PAR_RING] = {};
     int par_pos = 0;
     double *state_rows = nullptr;                  // 8 per boundary, for the asynchronous read
@@ -538,15 +538,15 @@ lbm_status lbm_set_0d_params(lbm_handle *h, int inst, int bc, const double *p, i
     for (int k = 0; k < np; k++) bp.par[k] = p[k];
     CK(h, cudaSetDevice(h->device));
     if (!h->par_ring) {
-        CK(h, cudaHostAlloc((void **)&h->par_ring, lbm_handle::PAR_RING * sizeof(BcParam), cudaHostAllocDefault));
+        CK(h, cudaHostAlloc((void **)&h->par_ring, lbm_handle::PAR_RING * sizeof(BcParam), cudaHostAllocMapped));
+        CK(h, cudaHostGetDevicePointer((void **)&h->par_ring_dev, h->par_ring, 0));
         for (int k = 0; k < lbm_handle::PAR_RING; k++)
             CK(h, cudaEventCreateWithFlags(&h->par_ev[k], cudaEventDisableTiming));
     }
     const int slot = h->par_pos++ % lbm_handle::PAR_RING;
     CK(h, cudaEventSynchronize(h->par_ev[slot]));  // the copy that last used this slot has run
     h->par_ring[slot] = bp;
-    CK(h, cudaMemcpyAsync(&h->bc_par[ip.bc_first + bc], &h->par_ring[slot], sizeof(BcParam),
-                          cudaMemcpyHostToDevice, h->stream));
+    CK(h, launch_copy_words(&h->par_ring_dev[slot], &h->bc_par[ip.bc_first + bc], sizeof(BcParam), h->stream));
     CK(h, cudaEventRecord(h->par_ev[slot], h->stream));
     return LBM_OK;
 }
@@ -556,6 +556,15 @@ lbm_status lbm_read_0d_state_async(lbm_handle *h, int inst, double *out) {
     const InstParam &ip = h->L.inst[inst];
     if (ip.n_bc == 0) return LBM_OK;
     CK(h, cudaSetDevice(h->device));
+    // page-locked host memory that the device can address: the kernel writes
+    // the rows there itself; otherwise through a device buffer and a copy
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, out) == cudaSuccess && at.type == cudaMemoryTypeHost && at.devicePointer) {
+        CK(h, launch_state_rows(h->bc_state, h->bc_par, h->etab, ip.bc_first, ip.n_bc, (int)h->L.bc.size(),
+                                (long long)h->steps, static_cast<double *>(at.devicePointer), h->stream));
+        return LBM_OK;
+    }
+    (void)cudaGetLastError();
     if (!h->state_rows) CK(h, dalloc(h, &h->state_rows, 8 * std::max<size_t>(1, h->L.bc.size())));
     double *rows = h->state_rows + 8 * (size_t)ip.bc_first;
     CK(h, launch_state_rows(h->bc_state, h->bc_par, h->etab, ip.bc_first, ip.n_bc, (int)h->L.bc.size(),

@@ -406,6 +406,22 @@ cudaError_t launch_state_rows(const BcState *st, const BcParam *par, const doubl
     return cudaGetLastError();
 }
 
+// Small stream-ordered transfer in 8-byte words, between mapped page-locked
+// host memory and device memory, on the compute engine (no hand-off to a
+// copy engine and back).
+__global__ void k_copy_words(const unsigned long long *__restrict__ src, unsigned long long *__restrict__ dst,
+                             int n) {
+    for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
+}
+
+cudaError_t launch_copy_words(const void *src, void *dst, size_t bytes, cudaStream_t s) {
+    if (bytes == 0) return cudaSuccess;
+    if (bytes % 8 != 0) return cudaErrorInvalidValue;
+    k_copy_words<<<1, 32, 0, s>>>(static_cast<const unsigned long long *>(src), static_cast<unsigned long long *>(dst),
+                                  (int)(bytes / 8));
+    return cudaGetLastError();
+}
+
 // compact -> box scatter of the gathered P, j into FP32 device arrays
 __global__ void k_scatter_box(const double *__restrict__ mac4, int M, const int32_t *__restrict__ box, float *P,
                               float *jx, float *jy, float *jz) {

@@ -168,3 +168,18 @@ def test_async_0d_state_read_equals_sync(Lattice):
     for bc in range(2):
         assert np.array_equal(got[bc], lat.state_0d(0, bc))
     assert bufs[0].numpy()[0] == 37.0 and bufs[1].numpy()[0] == 74.0
+
+
+def test_async_0d_state_read_into_pageable_memory(Lattice):
+    # memory the device cannot address goes through the device buffer and a
+    # copy; the values are the same as the direct write into pinned memory
+    torch = pytest.importorskip("torch")
+    inst = configs.lv_tube(period=300)
+    lat = Lattice([inst], precision="f32")
+    lat.step(50)
+    pinned = torch.zeros(16, dtype=torch.float64, pin_memory=True)
+    pageable = np.zeros(16)
+    lat.state_0d_async(0, pinned.data_ptr())
+    lat.state_0d_async(0, pageable.ctypes.data)
+    lat.sync()
+    assert pageable[0] == 50.0 and np.array_equal(pageable, pinned.numpy())
