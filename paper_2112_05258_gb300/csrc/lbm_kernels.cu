@@ -1,10 +1,12 @@
 // Device kernels of the per-step hot path besides the fused stream-collide
 // (lbm_stream_collide.cu) and the immersed boundary (lbm_ib.cu):
 //   k_bc_reduce       deterministic FP64 partial sums of the boundary flow Q
-//                     and pressure over the first fluid layer of each 0D boundary
+//                     and gauge pressure over the first fluid layer of each
+//                     0D boundary (per-cell terms in the compute type)
 //   k_bc_apply        the FP64 forward-Euler 0D step (Eqs. rightbc, rightQ,
 //                     LVE; valve switch and smoothing of Section 2.2.1) and
-//                     the ghost populations of Eq. Non-equilibrium3
+//                     the ghost populations of Eq. Non-equilibrium3 (per link,
+//                     in the compute type)
 //   k_gather          read-out of f(t_n), P and j for the host
 //   k_wall_shear      wall shear stress at the fluid cells next to rigid walls
 //   k_init, k_init_eq inverse of the pull: lays out a given f(t_0), or the
@@ -26,24 +28,28 @@ __constant__ signed char c_ey[NQ] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0
 __constant__ signed char c_ez[NQ] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
 
 // ---------------------------------------------------------------------------
-// 0D coupling.  One CTA per boundary.
+// 0D coupling.  The per-cell and per-link arithmetic runs in the compute type
+// R of the populations (FP32 for FP32/FP16/BF16 storage: the FP64 pipe of
+// this part is narrow), with pressures as deviations from P_ref = 1/3 so that
+// FP32 keeps their resolution; the boundary sums and the 0D step are FP64.
 template <class R>
-__device__ __forceinline__ void forced_velocity(const KParams &p, int cf, double v[3]) {
+__device__ __forceinline__ void forced_velocity(const KParams &p, int cf, R v[3]) {
     const size_t N = (size_t)p.n;
     const R *aux = static_cast<const R *>(p.aux);
-    v[0] = (double)aux[N + cf];
-    v[1] = (double)aux[2 * N + cf];
-    v[2] = (double)aux[3 * N + cf];
+    v[0] = aux[N + cf];
+    v[1] = aux[2 * N + cf];
+    v[2] = aux[3 * N + cf];
     if (__ldg(&p.flags[cf]) & FL_BAND) {
         const typename Vec4<R>::T bb = static_cast<const typename Vec4<R>::T *>(p.b)[cf];
-        v[0] += 0.5 * (double)bb.x;
-        v[1] += 0.5 * (double)bb.y;
-        v[2] += 0.5 * (double)bb.z;
+        v[0] += R(0.5) * bb.x;
+        v[1] += R(0.5) * bb.y;
+        v[2] += R(0.5) * bb.z;
     }
 }
 
-// Partial sums of the boundary flow Q = sum n.j / sum f and of the pressure
-// over one chunk of a boundary's first fluid layer (FP64, fixed tree order).
+// Partial sums of the boundary flow Q = sum n.j / sum f and of the gauge
+// pressure (P - P_ref = c_s^2 sum s) over one chunk of a boundary's first
+// fluid layer (FP64 sums in a fixed tree order).
 template <class R>
 __global__ void __launch_bounds__(BC_CHUNK) k_bc_reduce(KParams p, BcKParams q) {
     const int b = q.red_bc[blockIdx.x], ch = q.red_chunk[blockIdx.x];
@@ -55,9 +61,9 @@ __global__ void __launch_bounds__(BC_CHUNK) k_bc_reduce(KParams p, BcKParams q) 
     double Q = 0.0, Ps = 0.0;
     if (a < P.n_xf) {
         const int cf = q.xf[P.xf_off + a];
-        const double sf = 1.0 + (double)aux[cf];
-        Q = (double)P.sign * (double)aux[(size_t)(1 + P.axis) * N + cf] / sf;
-        Ps = sf / 3.0;
+        const R sd = aux[cf];
+        Q = (double)((R)P.sign * aux[(size_t)(1 + P.axis) * N + cf] / (R(1) + sd));
+        Ps = (double)(sd / R(3));
     }
     sQ[threadIdx.x] = Q;
     sP[threadIdx.x] = Ps;
@@ -87,7 +93,7 @@ __global__ void __launch_bounds__(BC_CHUNK) k_bc_apply(S *__restrict__ f, KParam
     const R *aux = static_cast<const R *>(p.aux);
     const int tid = threadIdx.x;
     const long long n = *p.step;
-    __shared__ double s_Pstar, s_S;
+    __shared__ double s_Pg, s_S, s_cos, s_sin;
     __shared__ int s_ptype, s_closed;
     if (tid < 32) {
         double Q = 0.0, Ps = 0.0;
@@ -103,7 +109,8 @@ __global__ void __launch_bounds__(BC_CHUNK) k_bc_apply(S *__restrict__ f, KParam
             const BcState old = q.state[(size_t)(n & 1) * q.n_bc_total + b];
             int ptype, closed;
             double Sm;
-            const BcState st = zero_d_step(P, old, Q, Ps, (double)P.n_xf, n, q.etab, &ptype, &closed, &Sm);
+            const double Psum = (double)P.n_xf / 3.0 + Ps;  // sum of P over the layer
+            const BcState st = zero_d_step(P, old, Q, Psum, (double)P.n_xf, n, q.etab, &ptype, &closed, &Sm);
             if (ch == 0) {
                 q.state[(size_t)((n + 1) & 1) * q.n_bc_total + b] = st;
                 double *w = q.wave + ((size_t)(n % q.wave_cap) * q.n_bc_total + b) * 4;
@@ -115,7 +122,12 @@ __global__ void __launch_bounds__(BC_CHUNK) k_bc_apply(S *__restrict__ f, KParam
             s_ptype = ptype;
             s_closed = closed;
             s_S = Sm;
-            s_Pstar = 1.0 / 3.0 + st.Pstar_gauge;
+            s_Pg = st.Pstar_gauge;
+            if (P.kind == BC_VELOCITY) {  // the inlet's phase, once for every link of the boundary
+                const double wv = P.par[0], tn1 = (double)(n + 1);
+                s_cos = cos(wv * tn1);
+                s_sin = sin(wv * tn1);
+            }
         }
     }
     __syncthreads();
@@ -124,48 +136,48 @@ __global__ void __launch_bounds__(BC_CHUNK) k_bc_apply(S *__restrict__ f, KParam
     const int cb = q.lk_xb[P.link_off + L];
     const int cf = q.lk_xf[P.link_off + L];
     const int i = q.lk_i[P.link_off + L];
-    const double Pf = (1.0 + (double)aux[cf]) / 3.0;
-    double vf[3];
+    R vf[3];
     forced_velocity<R>(p, cf, vf);
-    double Ps, vs[3];
+    R dP, vs[3];  // P* - P(x_f) and v*
     if (s_ptype) {  // pressure-type: (P_0D(t_{n+1}), v(x_f, t_n))
-        Ps = s_Pstar;
+        dP = (R)s_Pg - aux[cf] / R(3);
         vs[0] = vf[0];
         vs[1] = vf[1];
         vs[2] = vf[2];
     } else {        // velocity-type: (P(x_f, t_n), v_0D(t_{n+1}))
-        Ps = Pf;
-        vs[0] = vs[1] = vs[2] = 0.0;
+        dP = R(0);
+        vs[0] = vs[1] = vs[2] = R(0);
         if (P.kind == BC_VELOCITY) {
             const double *pr = q.profile + 3 * (size_t)(P.node_off + q.lk_node[P.link_off + L]);
-            const double wv = P.par[0], tn1 = (double)(n + 1);
-            vs[P.axis] = (double)P.sign * (pr[0] + pr[1] * cos(wv * tn1) - pr[2] * sin(wv * tn1));
+            vs[P.axis] = (R)((double)P.sign * (pr[0] + pr[1] * s_cos - pr[2] * s_sin));
         } else if (P.kind == BC_LV) {  // closed valve: v_0(T_d) S(t, T_d, N_S)
             double *v0 = q.v0 + 3 * (size_t)(P.xf_off + q.lk_xfi[P.link_off + L]);
-            double u0[3];
+            R u0[3];
             if (s_closed) {  // v_0(T_d) = v(x_f, T_d); links sharing x_f store the same value
-                u0[0] = v0[0] = vf[0];
-                u0[1] = v0[1] = vf[1];
-                u0[2] = v0[2] = vf[2];
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    u0[a] = vf[a];
+                    v0[a] = (double)vf[a];
+                }
             } else {
-                u0[0] = v0[0];
-                u0[1] = v0[1];
-                u0[2] = v0[2];
+#pragma unroll
+                for (int a = 0; a < 3; a++) u0[a] = (R)v0[a];
             }
-            vs[0] = u0[0] * s_S;
-            vs[1] = u0[1] * s_S;
-            vs[2] = u0[2] * s_S;
+            const R Sm = (R)s_S;
+            vs[0] = u0[0] * Sm;
+            vs[1] = u0[1] * Sm;
+            vs[2] = u0[2] * Sm;
         }
     }
-    const double ex = c_ex[i], ey = c_ey[i], ez = c_ez[i];
-    const double w = i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
-    const double eus = ex * vs[0] + ey * vs[1] + ez * vs[2];
-    const double euf = ex * vf[0] + ey * vf[1] + ez * vf[2];
-    const double us2 = vs[0] * vs[0] + vs[1] * vs[1] + vs[2] * vs[2];
-    const double uf2 = vf[0] * vf[0] + vf[1] * vf[1] + vf[2] * vf[2];
-    const double dfeq = w * 3.0 * (Ps - Pf) + w * (3.0 * (eus - euf) + 4.5 * (eus * eus - euf * euf) - 1.5 * (us2 - uf2));
-    const double post = (double)Storage<S>::ld(f + pidx(i, (uint32_t)cf, (uint32_t)N));
-    Storage<S>::st(f + pidx(i, (uint32_t)cb, (uint32_t)N), (R)(post + dfeq));
+    const R ex = c_ex[i], ey = c_ey[i], ez = c_ez[i];
+    const R w = i == 0 ? R(1.0 / 3.0) : (i < 7 ? R(1.0 / 18.0) : R(1.0 / 36.0));
+    const R eus = ex * vs[0] + ey * vs[1] + ez * vs[2];
+    const R euf = ex * vf[0] + ey * vf[1] + ez * vf[2];
+    const R us2 = vs[0] * vs[0] + vs[1] * vs[1] + vs[2] * vs[2];
+    const R uf2 = vf[0] * vf[0] + vf[1] * vf[1] + vf[2] * vf[2];
+    const R dfeq = w * R(3) * dP + w * (R(3) * (eus - euf) + R(4.5) * (eus * eus - euf * euf) - R(1.5) * (us2 - uf2));
+    const R post = Storage<S>::ld(f + pidx(i, (uint32_t)cf, (uint32_t)N));
+    Storage<S>::st(f + pidx(i, (uint32_t)cb, (uint32_t)N), post + dfeq);
 }
 
 // ---------------------------------------------------------------------------

@@ -25,7 +25,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="tube", choices=["tube", "aorta", "fil_tube", "spring_tube", "axi"])
+    ap.add_argument("--case", default="tube", choices=["tube", "aorta", "fil_tube", "spring_tube", "axi", "batch"])
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--precision", default="f32")
     ap.add_argument("--block", type=int, default=0)
@@ -44,14 +44,19 @@ def main():
               f"{(time.perf_counter() - t0) * 1e3:.1f} ms")
         lat.close()
         return
-    if args.case == "tube":
+    insts = None
+    if args.case == "batch":
+        from workloads import batch
+        insts, _ = batch.tube_batch(256, 0)
+        inst = insts[0]
+    elif args.case == "tube":
         inst = configs.rigid_tube(128, 128, 512, radius=40.0, period=4000)
     elif args.case in ("fil_tube", "spring_tube"):
         inst = configs.ib_tube(64, 64, 512, radius=24.0, period=4000, u_peak=0.02,
                                filaments=args.case == "fil_tube")
     else:
         inst = aorta.build(0)
-    lat = Lattice([inst], precision=args.precision, block_size=args.block,
+    lat = Lattice(insts or [inst], precision=args.precision, block_size=args.block,
                   graph_steps=2 * (args.steps + 1))  # graphs longer than the run: single-step graphs only
     info = lat.info()
     t0 = time.perf_counter()
