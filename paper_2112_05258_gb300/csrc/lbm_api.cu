@@ -48,6 +48,8 @@ struct lbm_handle {
     double *profile = nullptr, *etab = nullptr, *v0 = nullptr, *wave = nullptr;
     InstParam *inst_dev = nullptr;
     double *partial = nullptr;
+    int *arrived = nullptr;
+    BcStepResult *bc_result = nullptr;
     int32_t *red_bc = nullptr, *red_chunk = nullptr, *app_bc = nullptr, *app_chunk = nullptr;
     int32_t *band = nullptr, *node_inst = nullptr;
     double *ibX = nullptr, *ibVs = nullptr, *ibI = nullptr, *ibF = nullptr, *ibVf = nullptr;
@@ -414,6 +416,9 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
     std::vector<BcState> st2(st);
     st2.insert(st2.end(), st.begin(), st.end());  // [2][n_bc]: read n & 1, write (n + 1) & 1
     if (ok) ok = ck(upload(h, &h->bc_par, L.bc), "bc") && ck(upload(h, &h->bc_state, st2), "bc state");
+    if (ok) ok = ck(dalloc(h, &h->arrived, std::max<size_t>(1, L.bc.size())), "arrivals") &&
+                 ck(cudaMemset(h->arrived, 0, std::max<size_t>(1, L.bc.size()) * sizeof(int)), "arrivals") &&
+                 ck(dalloc(h, &h->bc_result, std::max<size_t>(1, L.bc.size())), "step results");
     if (ok) ok = ck(dalloc(h, &h->partial, 2 * std::max<size_t>(1, (size_t)L.n_partial)), "partials") &&
                  ck(upload(h, &h->red_bc, L.red_bc), "tables") && ck(upload(h, &h->red_chunk, L.red_chunk), "tables") &&
                  ck(upload(h, &h->app_bc, L.app_bc), "tables") && ck(upload(h, &h->app_chunk, L.app_chunk), "tables");
@@ -486,6 +491,15 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
     h->bp.wave = h->wave;
     h->bp.wave_cap = h->wave_cap;
     h->bp.partial = h->partial;
+    h->bp.arrived = h->arrived;
+    {
+        // the per-block 0D step costs nothing extra while the link blocks run
+        // in one wave (about 4 resident per SM); beyond that, once per boundary
+        int sms = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) sms = 1;
+        h->bp.step_in_reduce = (int)L.app_bc.size() > 4 * sms ? 1 : 0;
+    }
+    h->bp.result = h->bc_result;
     h->bp.n_red_blocks = (int)L.red_bc.size();
     h->bp.n_app_blocks = (int)L.app_bc.size();
     h->bp.red_bc = h->red_bc;

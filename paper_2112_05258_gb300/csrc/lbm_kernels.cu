@@ -2,11 +2,12 @@
 // (lbm_stream_collide.cu) and the immersed boundary (lbm_ib.cu):
 //   k_bc_reduce       deterministic FP64 partial sums of the boundary flow Q
 //                     and gauge pressure over the first fluid layer of each
-//                     0D boundary (per-cell terms in the compute type)
-//   k_bc_apply        the FP64 forward-Euler 0D step (Eqs. rightbc, rightQ,
-//                     LVE; valve switch and smoothing of Section 2.2.1) and
-//                     the ghost populations of Eq. Non-equilibrium3 (per link,
-//                     in the compute type)
+//                     0D boundary (per-cell terms in the compute type), then,
+//                     once per boundary, the FP64 forward-Euler 0D step (Eqs.
+//                     rightbc, rightQ, LVE; valve switch and smoothing of
+//                     Section 2.2.1)
+//   k_bc_apply        the ghost populations of Eq. Non-equilibrium3 (per
+//                     link, in the compute type)
 //   k_gather          read-out of f(t_n), P and j for the host
 //   k_wall_shear      wall shear stress at the fluid cells next to rigid walls
 //   k_init, k_init_eq inverse of the pull: lays out a given f(t_0), or the
@@ -47,9 +48,63 @@ __device__ __forceinline__ void forced_velocity(const KParams &p, int cf, R v[3]
     }
 }
 
+// The 0D step of boundary b from the sums over its first layer (taken by one
+// thread): the state of t_{n+1} and, if store, the state and the waveform row
+// written; returns what the ghost pass needs.
+static __device__ BcStepResult bc_step(const BcParam &P, int b, double Q, double Ps, long long n,
+                                       const BcKParams &q, bool store) {
+    const BcState old = q.state[(size_t)(n & 1) * q.n_bc_total + b];
+    int ptype, closed;
+    double Sm;
+    const double Psum = (double)P.n_xf / 3.0 + Ps;  // sum of P over the layer
+    const BcState st = zero_d_step(P, old, Q, Psum, (double)P.n_xf, n, q.etab, &ptype, &closed, &Sm);
+    if (store) {
+        q.state[(size_t)((n + 1) & 1) * q.n_bc_total + b] = st;
+        double *w = q.wave + ((size_t)(n % q.wave_cap) * q.n_bc_total + b) * 4;
+        w[0] = st.Qu;
+        w[1] = st.Pbar - 1.0 / 3.0;
+        w[2] = (P.kind == BC_RCR) ? st.Pw : (P.kind == BC_LV ? st.Pv : st.Pstar_gauge);
+        w[3] = st.valve_open;
+    }
+    BcStepResult r;
+    r.Pg = st.Pstar_gauge;
+    r.S = Sm;
+    r.cosp = r.sinp = 0.0;
+    if (P.kind == BC_VELOCITY) {  // the inlet's phase, once for every link of the boundary
+        const double wv = P.par[0], tn1 = (double)(n + 1);
+        r.cosp = cos(wv * tn1);
+        r.sinp = sin(wv * tn1);
+    }
+    r.ptype = ptype;
+    r.closed = closed;
+    r.pad0 = r.pad1 = 0;
+    return r;
+}
+
+// The boundary's partial sums added by one warp in a fixed order (lane k
+// takes partials k, k + 32, ..., then a butterfly), so that every caller gets
+// the same bits.
+static __device__ __forceinline__ void bc_sum_partials(const BcParam &P, const BcKParams &q, double *Q, double *Ps) {
+    const int lane = threadIdx.x & 31;
+    double a = 0.0, c = 0.0;
+    for (int k = lane; k < P.n_red; k += 32) {
+        a += __ldcg(&q.partial[2 * (P.red_off + k)]);
+        c += __ldcg(&q.partial[2 * (P.red_off + k) + 1]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    *Q = a;
+    *Ps = c;
+}
+
 // Partial sums of the boundary flow Q = sum n.j / sum f and of the gauge
 // pressure (P - P_ref = c_s^2 sum s) over one chunk of a boundary's first
-// fluid layer (FP64 sums in a fixed tree order).
+// fluid layer (FP64 sums in a fixed tree order).  With q.step_in_reduce (many
+// link blocks), the boundary's last chunk to arrive (a counter per boundary;
+// no block waits for another) sums all partials and takes the 0D step once
+// for the boundary; otherwise every link block of k_bc_apply takes it.
 template <class R>
 __global__ void __launch_bounds__(BC_CHUNK) k_bc_reduce(KParams p, BcKParams q) {
     const int b = q.red_bc[blockIdx.x], ch = q.red_chunk[blockIdx.x];
@@ -58,6 +113,7 @@ __global__ void __launch_bounds__(BC_CHUNK) k_bc_reduce(KParams p, BcKParams q) 
     const R *aux = static_cast<const R *>(p.aux);
     const int a = ch * BC_CHUNK + threadIdx.x;
     __shared__ double sQ[BC_CHUNK], sP[BC_CHUNK];
+    __shared__ int s_last;
     double Q = 0.0, Ps = 0.0;
     if (a < P.n_xf) {
         const int cf = q.xf[P.xf_off + a];
@@ -78,69 +134,59 @@ __global__ void __launch_bounds__(BC_CHUNK) k_bc_reduce(KParams p, BcKParams q) 
     if (threadIdx.x == 0) {
         q.partial[2 * (P.red_off + ch)] = sQ[0];
         q.partial[2 * (P.red_off + ch) + 1] = sP[0];
+        if (q.step_in_reduce) {
+            __threadfence();  // the partial is visible before the arrival is counted
+            s_last = atomicAdd(&q.arrived[b], 1) == P.n_red - 1;
+        }
     }
+    if (!q.step_in_reduce) return;
+    __syncthreads();
+    if (!s_last || threadIdx.x >= 32) return;
+    __threadfence();
+    bc_sum_partials(P, q, &Q, &Ps);
+    if (threadIdx.x != 0) return;
+    q.arrived[b] = 0;  // for the next step (kernel boundaries order it)
+    q.result[b] = bc_step(P, b, Q, Ps, *p.step, q, true);
 }
 
 // Ghost populations of one chunk of links, Eq. Non-equilibrium3 written as
 //   f_i(x_b) = f*_i(x_f) + f^eq_i(P*, v*) - f^eq_i(P(x_f), v(x_f)),
 // since f*_i(x_f) = f^eq_i + (1 - 1/tau) f^neq_i + F_i at x_f.
-template <class S>
+// STEP_HERE: the kernel for few link blocks, each of which takes the 0D step
+// itself (the boundary's first chunk storing the state); otherwise the step's
+// result comes from k_bc_reduce.  Two instances, so that the one without the
+// step keeps its low register count.
+template <class S, bool STEP_HERE>
 __global__ void __launch_bounds__(BC_CHUNK) k_bc_apply(S *__restrict__ f, KParams p, BcKParams q) {
     using R = typename Storage<S>::R;
     const int b = q.app_bc[blockIdx.x], ch = q.app_chunk[blockIdx.x];
     const BcParam &P = q.par[b];
     const size_t N = (size_t)p.n;
     const R *aux = static_cast<const R *>(p.aux);
-    const int tid = threadIdx.x;
-    const long long n = *p.step;
-    __shared__ double s_Pg, s_S, s_cos, s_sin;
-    __shared__ int s_ptype, s_closed;
-    if (tid < 32) {
-        double Q = 0.0, Ps = 0.0;
-        for (int k = tid; k < P.n_red; k += 32) {
-            Q += q.partial[2 * (P.red_off + k)];
-            Ps += q.partial[2 * (P.red_off + k) + 1];
+    const int L = ch * BC_CHUNK + threadIdx.x;
+    BcStepResult r;
+    if (!STEP_HERE) {
+        if (L >= P.n_links) return;
+        r = q.result[b];
+    } else {
+        __shared__ BcStepResult s_r;
+        if (threadIdx.x < 32) {
+            double Q, Ps;
+            bc_sum_partials(P, q, &Q, &Ps);
+            if (threadIdx.x == 0) s_r = bc_step(P, b, Q, Ps, *p.step, q, ch == 0);
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            Q += __shfl_xor_sync(0xffffffffu, Q, o);
-            Ps += __shfl_xor_sync(0xffffffffu, Ps, o);
-        }
-        if (tid == 0) {
-            const BcState old = q.state[(size_t)(n & 1) * q.n_bc_total + b];
-            int ptype, closed;
-            double Sm;
-            const double Psum = (double)P.n_xf / 3.0 + Ps;  // sum of P over the layer
-            const BcState st = zero_d_step(P, old, Q, Psum, (double)P.n_xf, n, q.etab, &ptype, &closed, &Sm);
-            if (ch == 0) {
-                q.state[(size_t)((n + 1) & 1) * q.n_bc_total + b] = st;
-                double *w = q.wave + ((size_t)(n % q.wave_cap) * q.n_bc_total + b) * 4;
-                w[0] = st.Qu;
-                w[1] = st.Pbar - 1.0 / 3.0;
-                w[2] = (P.kind == BC_RCR) ? st.Pw : (P.kind == BC_LV ? st.Pv : st.Pstar_gauge);
-                w[3] = st.valve_open;
-            }
-            s_ptype = ptype;
-            s_closed = closed;
-            s_S = Sm;
-            s_Pg = st.Pstar_gauge;
-            if (P.kind == BC_VELOCITY) {  // the inlet's phase, once for every link of the boundary
-                const double wv = P.par[0], tn1 = (double)(n + 1);
-                s_cos = cos(wv * tn1);
-                s_sin = sin(wv * tn1);
-            }
-        }
+        __syncthreads();
+        if (L >= P.n_links) return;
+        r = s_r;
     }
-    __syncthreads();
-    const int L = ch * BC_CHUNK + tid;
-    if (L >= P.n_links) return;
     const int cb = q.lk_xb[P.link_off + L];
     const int cf = q.lk_xf[P.link_off + L];
     const int i = q.lk_i[P.link_off + L];
     R vf[3];
     forced_velocity<R>(p, cf, vf);
     R dP, vs[3];  // P* - P(x_f) and v*
-    if (s_ptype) {  // pressure-type: (P_0D(t_{n+1}), v(x_f, t_n))
-        dP = (R)s_Pg - aux[cf] / R(3);
+    if (r.ptype) {  // pressure-type: (P_0D(t_{n+1}), v(x_f, t_n))
+        dP = (R)r.Pg - aux[cf] / R(3);
         vs[0] = vf[0];
         vs[1] = vf[1];
         vs[2] = vf[2];
@@ -149,11 +195,11 @@ __global__ void __launch_bounds__(BC_CHUNK) k_bc_apply(S *__restrict__ f, KParam
         vs[0] = vs[1] = vs[2] = R(0);
         if (P.kind == BC_VELOCITY) {
             const double *pr = q.profile + 3 * (size_t)(P.node_off + q.lk_node[P.link_off + L]);
-            vs[P.axis] = (R)((double)P.sign * (pr[0] + pr[1] * s_cos - pr[2] * s_sin));
+            vs[P.axis] = (R)((double)P.sign * (pr[0] + pr[1] * r.cosp - pr[2] * r.sinp));
         } else if (P.kind == BC_LV) {  // closed valve: v_0(T_d) S(t, T_d, N_S)
             double *v0 = q.v0 + 3 * (size_t)(P.xf_off + q.lk_xfi[P.link_off + L]);
             R u0[3];
-            if (s_closed) {  // v_0(T_d) = v(x_f, T_d); links sharing x_f store the same value
+            if (r.closed) {  // v_0(T_d) = v(x_f, T_d); links sharing x_f store the same value
 #pragma unroll
                 for (int a = 0; a < 3; a++) {
                     u0[a] = vf[a];
@@ -163,7 +209,7 @@ __global__ void __launch_bounds__(BC_CHUNK) k_bc_apply(S *__restrict__ f, KParam
 #pragma unroll
                 for (int a = 0; a < 3; a++) u0[a] = (R)v0[a];
             }
-            const R Sm = (R)s_S;
+            const R Sm = (R)r.S;
             vs[0] = u0[0] * Sm;
             vs[1] = u0[1] * Sm;
             vs[2] = u0[2] * Sm;
@@ -377,7 +423,11 @@ cudaError_t launch_boundary(int prec, void *f, const KParams &p, const BcKParams
     if (q.n_bc_total == 0) return cudaSuccess;
     if (prec == 3) k_bc_reduce<double><<<q.n_red_blocks, BC_CHUNK, 0, s>>>(p, q);
     else k_bc_reduce<float><<<q.n_red_blocks, BC_CHUNK, 0, s>>>(p, q);
-    DISPATCH(prec, (k_bc_apply<S><<<q.n_app_blocks, BC_CHUNK, 0, s>>>(as<S>(f), p, q)));
+    if (q.step_in_reduce) {
+        DISPATCH(prec, (k_bc_apply<S, false><<<q.n_app_blocks, BC_CHUNK, 0, s>>>(as<S>(f), p, q)));
+    } else {
+        DISPATCH(prec, (k_bc_apply<S, true><<<q.n_app_blocks, BC_CHUNK, 0, s>>>(as<S>(f), p, q)));
+    }
     return cudaGetLastError();
 }
 

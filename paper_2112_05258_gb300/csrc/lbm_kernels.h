@@ -30,9 +30,19 @@ struct KParams {
 // 0D boundary tables (device memory).  The boundary work of a step runs as
 // two kernels: k_bc_reduce (one CTA per chunk of BC_CHUNK first-layer cells
 // writes an FP64 partial sum) and k_bc_apply (one CTA per chunk of BC_CHUNK
-// links: every CTA of a boundary sums the partials in the same fixed order,
-// evaluates the same 0D step from the state of t_n, and writes its ghosts;
-// the boundary's first CTA stores the state of t_{n+1}).
+// links writes the ghosts).  The 0D step from the state of t_n (the partials
+// summed in a fixed order) is taken either by the boundary's last reduce CTA
+// to finish, which stores the state of t_{n+1} and the step's result, or,
+// when the link CTAs fit in one wave, by every link CTA (the boundary's first
+// one storing the state): the same arithmetic either way.
+struct BcStepResult {
+    double Pg;          // P* - P_ref of a pressure-type coupling
+    double S;           // smoothing factor S(t_{n+1}) of a closed LV valve
+    double cosp, sinp;  // velocity inlet: cos and sin of omega t_{n+1}
+    int ptype;          // 1: pressure-type ghosts, 0: velocity-type
+    int closed;         // 1: the LV valve closed in this step
+    int pad0, pad1;
+};
 struct BcKParams {
     int n_bc_total;
     const BcParam *par;
@@ -45,7 +55,10 @@ struct BcKParams {
     double *v0;                 // 3 per first-layer entry
     double *wave;               // ring buffer [cap][n_bc_total][4]
     int wave_cap;
-    double *partial;            // 2 per reduce chunk: sum n.j/sum f, sum P
+    double *partial;            // 2 per reduce chunk: sum n.j/sum f, sum (P - P_ref)
+    int step_in_reduce;         // 1: the 0D step once per boundary in k_bc_reduce; 0: in every k_bc_apply block
+    int *arrived;               // per boundary: reduce CTAs done in this step (back to 0 after it)
+    BcStepResult *result;       // per boundary
     int n_red_blocks, n_app_blocks;
     const int32_t *red_bc, *red_chunk;  // per reduce block
     const int32_t *app_bc, *app_chunk;  // per apply block

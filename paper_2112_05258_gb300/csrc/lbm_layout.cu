@@ -245,7 +245,7 @@ std::string build_layout(const lbm_config *cfg, Layout &L) {
     // block tables of the boundary kernels
     for (size_t b = 0; b < L.bc.size(); b++) {
         BcParam &bp = L.bc[b];
-        bp.n_red = (bp.n_xf + BC_CHUNK - 1) / BC_CHUNK;
+        bp.n_red = std::max(1, (bp.n_xf + BC_CHUNK - 1) / BC_CHUNK);  // one at least: it takes the 0D step
         bp.red_off = (int)L.n_partial;
         L.n_partial += bp.n_red;
         for (int k = 0; k < bp.n_red; k++) {

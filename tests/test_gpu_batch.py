@@ -183,3 +183,20 @@ def test_async_0d_state_read_into_pageable_memory(Lattice):
     lat.state_0d_async(0, pageable.ctypes.data)
     lat.sync()
     assert pageable[0] == 50.0 and np.array_equal(pageable, pinned.numpy())
+
+
+def test_once_per_boundary_0d_step_equals_per_block(Lattice):
+    # a batch whose link blocks exceed one wave (64 uneven LV tubes: about
+    # 1,400 blocks) takes each boundary's 0D step once, in the last reduction
+    # block to arrive; a single tube takes it in every link block.  The sums
+    # and the step are the same arithmetic, so the bits agree.
+    insts, _ = batch.tube_batch(64, 3)
+    big = Lattice(insts, precision="f32", wave_capacity=512)
+    big.step(150)
+    big.sync()
+    for q in (0, 17, 63):
+        single = Lattice([insts[q]], precision="f32", wave_capacity=512)
+        single.step(150)
+        assert np.array_equal(big.waves(q), single.waves(0))
+        assert np.array_equal(big.populations(q), single.populations(0))
+        single.close()
