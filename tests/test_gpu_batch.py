@@ -106,7 +106,10 @@ def test_uneven_batch_equals_single(Lattice):
 
 @pytest.mark.parametrize("variant", range(5))
 def test_every_stream_collide_variant_gives_the_trajectory(Lattice, variant):
-    # the occupancy and cells-per-thread variants run the same per-cell arithmetic
+    # the occupancy and cells-per-thread variants run the same per-cell
+    # arithmetic: the instance without wall nodes agrees bit for bit in FP32;
+    # the second has wall nodes, whose spreading atomics add in run order, and
+    # agrees to rounding under any variant
     insts = [configs.lv_tube(period=300), configs.ib_tube()]
     ref = Lattice(insts, precision="f64")
     ref.step(120)
@@ -116,12 +119,15 @@ def test_every_stream_collide_variant_gives_the_trajectory(Lattice, variant):
     for q in range(2):
         assert np.abs(lat.populations(q) - ref.populations(q)).max() < 1e-14
         assert np.abs(lat.waves(q)[:, 1:] - ref.waves(q)[:, 1:]).max() < 1e-14
-    f32 = Lattice(insts, precision="f16")
-    f32.set_stream_collide_shape(128, variant)
-    f32.step(60)
-    g32 = Lattice(insts, precision="f16")
-    g32.step(60)
-    assert np.abs(f32.populations(0) - g32.populations(0)).max() < 1e-6
+    tols = {"f16": (1e-6, 4e-5), "f32": (0.0, 2e-7)}
+    for prec, tol in tols.items():
+        a = Lattice(insts, precision=prec)
+        a.set_stream_collide_shape(128, variant)
+        a.step(60)
+        b = Lattice(insts, precision=prec)
+        b.step(60)
+        for q in range(2):
+            assert np.abs(a.populations(q) - b.populations(q)).max() <= tol[q], (prec, q)
 
 
 def test_set_0d_params_is_stream_ordered(Lattice):
