@@ -8,7 +8,8 @@
 //   k_axi_init     inverse of the pull (lays out a given f(t_0))
 //   k_axi_bc       one CTA: for every 0D boundary the FP64 area-weighted
 //                  flow and pressure of its first fluid layer, the 0D step
-//                  and the ghost populations of Eq. Non-equilibrium3
+//                  and the ghost populations of Eq. Non-equilibrium3 (per
+//                  node and per link in the compute type)
 //
 // Sources (derived from the axisymmetric incompressible equations, rho0 = 1;
 // the printed h^(2) of Eq. AH1 is not legible): with j = sum e f (the
@@ -220,10 +221,14 @@ __global__ void k_axi_init(S *__restrict__ fout, Params p, const double *__restr
     }
 }
 
-__device__ __forceinline__ double feq_dev(int i, double sp, double vx, double vr) {
-    // f^eq_i - w_i for 3P - 1 = sp
-    const double eu = ex(i) * vx + er(i) * vr;
-    return wgt(i) * (sp + 3.0 * eu + 4.5 * eu * eu - 1.5 * (vx * vx + vr * vr));
+// f^eq_i(P*, v*) - f^eq_i(P, v) with 3P - 1 = sp (in the compute type R)
+template <class R>
+__device__ __forceinline__ R dfeq_dev(int i, R sps, R vxs, R vrs, R spf, R vxf, R vrf) {
+    const R eus = R(ex(i)) * vxs + R(er(i)) * vrs, euf = R(ex(i)) * vxf + R(er(i)) * vrf;
+    const R w = (R)wgt(i);
+    return w * (sps - spf) +
+           w * (R(3) * (eus - euf) + R(4.5) * (eus * eus - euf * euf) -
+                R(1.5) * ((vxs * vxs + vrs * vrs) - (vxf * vxf + vrf * vrf)));
 }
 
 // All boundaries in one CTA (they are small in 2D): area-weighted FP64 sums
@@ -231,6 +236,9 @@ __device__ __forceinline__ double feq_dev(int i, double sp, double vx, double vr
 // closure velocities, and the ghosts of Eq. Non-equilibrium3 written as
 //   f_i(x_b) = f*_i'(x_f) + f^eq_i'(P*, v*) - f^eq_i'(P(x_f), v(x_f)),
 // i' the direction arriving at x_f (mirrored for links across the axis).
+// Per-node and per-link terms run in the compute type R with pressures as
+// deviations from P_ref (the FP64 pipe of this part is narrow); the sums and
+// the 0D step are FP64.
 template <class S>
 __global__ void __launch_bounds__(256) k_axi_bc(S *__restrict__ f, Params p, BcDev q) {
     using R = typename Storage<S>::R;
@@ -238,19 +246,19 @@ __global__ void __launch_bounds__(256) k_axi_bc(S *__restrict__ f, Params p, BcD
     const int n = p.n;
     const long long t = *q.step;
     __shared__ double sQ[256], sP[256];
-    __shared__ double sh_Pstar, sh_S;
+    __shared__ double sh_Pstar, sh_S, sh_cos, sh_sin;
     __shared__ int sh_ptype, sh_closed;
     const int width = 1 + 4 * q.n_bc;
     double *row = q.wave + (size_t)(t % q.wave_cap) * width;
     if (threadIdx.x == 0) row[0] = (double)t;
     for (int b = 0; b < q.n_bc; b++) {
         const BcParam &P = q.par[b];
-        double Q = 0.0, Ps = 0.0;
+        double Q = 0.0, Ps = 0.0;  // Ps: sum of A (P - P_ref)
         for (int a = threadIdx.x; a < q.xf_n[b]; a += blockDim.x) {
             const int cf = q.xf[q.xf_off[b] + a];
-            const double A = q.area[q.xf_off[b] + a];
-            Q += A * (double)P.sign * (double)aux[n + cf] / (1.0 + (double)aux[5 * n + cf]);
-            Ps += A * (1.0 + (double)aux[cf]) / 3.0;
+            const R A = (R)q.area[q.xf_off[b] + a];
+            Q += (double)(A * (R)P.sign * aux[n + cf] / (R(1) + aux[5 * n + cf]));
+            Ps += (double)(A * aux[cf] / R(3));
         }
         sQ[threadIdx.x] = Q;
         sP[threadIdx.x] = Ps;
@@ -265,12 +273,18 @@ __global__ void __launch_bounds__(256) k_axi_bc(S *__restrict__ f, Params p, BcD
         if (threadIdx.x == 0) {
             int ptype, closed;
             double Sm;
-            const BcState st = zero_d_step(P, q.state[b], sQ[0], sP[0], q.area_sum[b], t, q.etab, &ptype, &closed, &Sm);
+            const double Psum = q.area_sum[b] / 3.0 + sP[0];  // sum of A P over the layer
+            const BcState st = zero_d_step(P, q.state[b], sQ[0], Psum, q.area_sum[b], t, q.etab, &ptype, &closed, &Sm);
             q.state[b] = st;
             sh_Pstar = st.Pstar_gauge;
             sh_ptype = ptype;
             sh_closed = closed;
             sh_S = Sm;
+            if (P.kind == BC_VELOCITY) {  // the inlet's phase, once for every link
+                const double w = P.par[0], tn1 = (double)(t + 1);
+                sh_cos = cos(w * tn1);
+                sh_sin = sin(w * tn1);
+            }
             row[1 + 4 * b] = st.Qu;
             row[2 + 4 * b] = st.Pbar - 1.0 / 3.0;
             row[3 + 4 * b] = P.kind == BC_RCR ? st.Pw : (P.kind == BC_LV ? st.Pv : st.Pstar_gauge);
@@ -284,31 +298,28 @@ __global__ void __launch_bounds__(256) k_axi_bc(S *__restrict__ f, Params p, BcD
                 q.v0[2 * (q.xf_off[b] + a) + 1] = (double)aux[4 * n + cf];
             }
         __syncthreads();
-        const double tn1 = (double)(t + 1);
         for (int L = threadIdx.x; L < q.lk_n[b]; L += blockDim.x) {
             const int g = q.lk_off[b] + L;
             const int cf = q.lk_xf[g], ie = q.lk_ieff[g];
-            const double spf = (double)aux[cf], vxf = (double)aux[3 * n + cf], vrf = (double)aux[4 * n + cf];
-            double sps, vxs, vrs;
+            const R spf = aux[cf], vxf = aux[3 * n + cf], vrf = aux[4 * n + cf];
+            R sps, vxs, vrs;
             if (sh_ptype) {
-                sps = 3.0 * sh_Pstar;  // 3 P* - 1 with P* = P_ref + P*_gauge
+                sps = (R)(3.0 * sh_Pstar);  // 3 P* - 1 with P* = P_ref + P*_gauge
                 vxs = vxf;
                 vrs = vrf;
             } else if (P.kind == BC_VELOCITY) {
                 const double *pr = q.profile + 3 * (size_t)(q.node_off[b] + q.lk_node[g]);
-                const double w = P.par[0];
                 sps = spf;
-                vxs = (double)P.sign * (pr[0] + pr[1] * cos(w * tn1) - pr[2] * sin(w * tn1));
-                vrs = 0.0;
+                vxs = (R)((double)P.sign * (pr[0] + pr[1] * sh_cos - pr[2] * sh_sin));
+                vrs = R(0);
             } else {
                 const double *v0 = q.v0 + 2 * (size_t)(q.xf_off[b] + q.lk_xfi[g]);
                 sps = spf;
-                vxs = v0[0] * sh_S;
-                vrs = v0[1] * sh_S;
+                vxs = (R)(v0[0] * sh_S);
+                vrs = (R)(v0[1] * sh_S);
             }
-            const double ghost = (double)Storage<S>::ld(f + (size_t)ie * n + cf) + feq_dev(ie, sps, vxs, vrs) -
-                                 feq_dev(ie, spf, vxf, vrf);
-            Storage<S>::st(f + (size_t)q.lk_ib[g] * n + q.lk_xb[g], (R)ghost);
+            const R ghost = Storage<S>::ld(f + (size_t)ie * n + cf) + dfeq_dev<R>(ie, sps, vxs, vrs, spf, vxf, vrf);
+            Storage<S>::st(f + (size_t)q.lk_ib[g] * n + q.lk_xb[g], ghost);
         }
         __syncthreads();
     }

@@ -29,19 +29,26 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--precision", default="f32")
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--nd", type=int, default=512, help="axi: nodes per diameter of the straight aorta")
+    ap.add_argument("--warmup", type=int, default=0, help="steps run before the timed ones")
     args = ap.parse_args()
     from paper_2112_05258_gb300 import Lattice
     from workloads import aorta, configs
     if args.case == "axi":
         from paper_2112_05258_gb300.axisym import AxiLattice
         from workloads import axisym
-        inst = axisym.straight_aorta(512)
-        lat = AxiLattice(inst, precision=args.precision, graph_steps=2 * (args.steps + 1))
+        inst = axisym.straight_aorta(args.nd)
+        gs = 64 if args.warmup else 2 * (args.steps + 1)  # timed runs: graphs of 64 steps
+        lat = AxiLattice(inst, precision=args.precision, graph_steps=gs)
+        if args.warmup:
+            lat.step(args.warmup)
+            lat.sync()
         t0 = time.perf_counter()
         lat.step(args.steps)
         lat.sync()
-        print(f"axi {args.precision}: nodes {inst.node.size} steps {args.steps} in "
-              f"{(time.perf_counter() - t0) * 1e3:.1f} ms")
+        dt = time.perf_counter() - t0
+        print(f"axi D/{args.nd} {args.precision}: nodes {inst.node.size} steps {args.steps} in "
+              f"{dt * 1e3:.1f} ms = {dt / args.steps * 1e3:.4f} ms per step")
         lat.close()
         return
     insts = None
