@@ -92,6 +92,14 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib) {
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int s = gt / TPN, q = gt % TPN;
     if (s >= ib.n_nodes) return;  // the lanes of a node leave together
+    if (q == 0) {  // lane 0 reads the node state after the gathers: bring it towards L2 meanwhile
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.Vs + 3 * s));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.I + 3 * s));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.X0 + 3 * s));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.ks + s));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.dA + s));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.pinned + s));
+    }
     const InstParam &ip = ib.inst[ib.node_inst[s]];
     double X[3];
     int i0[3];
