@@ -37,6 +37,7 @@ __global__ void k_band_moments(const S *__restrict__ fin, KParams p, IbKParams i
     for (int i = 1; i < NQ; i++) {
         size_t idx;
         if (fl & (1u << i)) idx = pidx(opp(i), (uint32_t)c, (uint32_t)N);
+        else if (nbk(i) == 4) idx = pidx(i, (uint32_t)(c - cx(i)), (uint32_t)N);  // along x: the own row
         else idx = pidx(i, (uint32_t)(p.rows[r].nb[nbk(i)] + x - cx(i)), (uint32_t)N);
         const R fi = Storage<S>::ld(fin + idx);
         if (cx(i)) jx += cx(i) * fi;

@@ -49,6 +49,7 @@ __global__ void __launch_bounds__(256, MINB)
             uint32_t off;
             if (i == 0) off = pidx(0, (uint32_t)c, N);
             else if (fl[u] & (1u << i)) off = pidx(opp(i), (uint32_t)c, N);
+            else if (nbk(i) == 4) off = pidx(i, (uint32_t)(c - cx(i)), N);  // along x: the own row, no table
             else off = pidx(i, (uint32_t)(__ldg(&nb[nbk(i)]) + x - cx(i)), N);
             f[u][i] = Storage<S>::ld(fin + off);
         }
