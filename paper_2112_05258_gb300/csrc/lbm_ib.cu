@@ -101,8 +101,10 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib) {
         asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.dA + s));
         asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.pinned + s));
     }
-    // the support-line table (36 entries) is read once the node's cell is known
+    // the support-line table (36 entries) and the fluid mask are read once
+    // the node's cell is known
     asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.lines + 36 * (size_t)s + (36 / TPN) * q));
+    if (q == 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.mask + 4 * (size_t)s));
     const InstParam &ip = ib.inst[ib.node_inst[s]];
     double X[3];
     int i0[3];
