@@ -4,6 +4,7 @@ import math
 import numpy as np
 import pytest
 
+import golden_fixtures
 import oracle
 from workloads import profiles
 
@@ -11,7 +12,9 @@ from workloads import profiles
 
 
 def test_smooth_limits_and_monotone():
-    t0, LS = 0.5, 15 * 0.005          # the paper's example: T_d = 0.5 s, N_S = 15, dt = 0.005 s
+    ex = golden_fixtures.load("smoothing_example_section2_2_1.txt")  # T_d = 0.5 s, N_S = 15, dt = 0.005 s
+    t0, dt, ns = ex["t0_s"], ex["dt_s"], ex["N_S"]
+    LS = ns * dt
     assert oracle.smooth(t0 - 1e-9, t0, LS) == 1.0
     assert oracle.smooth(0.0, t0, LS) == 1.0
     assert oracle.smooth(t0, t0, LS) == 1.0
@@ -24,13 +27,16 @@ def test_smooth_limits_and_monotone():
     assert np.all((s[inner] > 0) & (s[inner] < 1))
     assert np.all(np.diff(s[inner]) < 0)   # strictly decreasing away from the flat ends
     # the 15 steps of the example stay strictly inside (0, 1] and reach 0 at the end
-    steps = [oracle.smooth(t0 + k * 0.005, t0, LS) for k in range(16)]
+    steps = [oracle.smooth(t0 + k * dt, t0, LS) for k in range(ns + 1)]
     assert steps[0] == 1.0 and steps[-1] == 0.0 and all(0 < x < 1 for x in steps[1:-1])
 
 
 def test_smooth_midpoint_value_and_flat_ends():
     # at u = 1/2 the definition gives exp(2 e^{-2} / (-1/2)) = exp(-4/e^2)
     assert oracle.smooth(1.5, 1.0, 1.0) == pytest.approx(math.exp(-4.0 / math.e ** 2), rel=1e-15)
+    ex = golden_fixtures.load("smoothing_example_section2_2_1.txt")
+    t0, LS = ex["t0_s"], ex["N_S"] * ex["dt_s"]
+    assert oracle.smooth(t0 + 0.5 * LS, t0, LS) == pytest.approx(math.exp(-4.0 / math.e ** 2), rel=1e-14)
     # C-infinity: one-sided slopes vanish at both ends of the window
     h = 1e-4
     d0 = (oracle.smooth(h, 0.0, 1.0) - 1.0) / h

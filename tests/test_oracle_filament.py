@@ -12,7 +12,9 @@
   the central-difference scheme predicts.
 """
 import numpy as np
+import pytest
 
+import golden_fixtures
 import oracle
 from workloads import IBNodes, Instance, geometry
 
@@ -80,7 +82,7 @@ def _mms_forcing(s, t):
     return np.stack([Bx, By, 0 * s], axis=-1)
 
 
-def _mms_error(N, dt, steps):
+def _mms_error(N, dt, steps, every=50):
     ds = 1.0 / N
     s = np.arange(N + 1) * ds
     Xm, X = _mms_X(s, -dt), _mms_X(s, 0.0)
@@ -92,9 +94,22 @@ def _mms_error(N, dt, steps):
         Xn = 2 * X - Xm + dt * dt * acc
         Xn[[0, -1]] = _mms_X(s[[0, -1]], t + dt)
         Xm, X = X, Xn
-        if n % 50 == 49:
+        if n % every == every - 1:
             err = max(err, np.abs(X - _mms_X(s, t + dt)).max())
     return err
+
+
+def test_mms_at_the_papers_setup_is_second_order():
+    # the paper's own run (Section 3.1): N = 25, 50, 100 elements, dt = 1e-5 s,
+    # 1e5 steps, the largest error over all nodes and every step
+    ex = golden_fixtures.load("mms_filament_section3_1.txt")
+    assert (ex["A_m"], ex["L_m"]) == (A, 1.0)
+    assert ex["E_Pa"] * ex["h_m"] == pytest.approx(EH, rel=1e-15)
+    assert ex["E_Pa"] * ex["h_m"] ** 3 / 12 == pytest.approx(EI, rel=1e-15)
+    Ns = [ex["N_coarsest"] * 2 ** k for k in range(ex["N_refinements"])]
+    errs = [_mms_error(N, ex["dt_s"], ex["steps"], every=1) for N in Ns]
+    rates = [np.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert all(abs(r - ex["expected_order"]) < 0.1 for r in rates), (errs, rates)
 
 
 def test_mms_second_order_in_space():
