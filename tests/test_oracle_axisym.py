@@ -14,6 +14,7 @@ axisymmetric pipe flow.
   tube.
 """
 import numpy as np
+import pytest
 from scipy import special
 
 import oracle.axisym as ax
@@ -106,3 +107,24 @@ def test_lv_inlet_cycles_on_axisymmetric_tube():
     assert opens >= 2 and closes >= 2
     # while the valve is open the inlet pressure follows the ventricle (pressure-type coupling)
     assert np.abs(w[valve == 1, 2]).max() > 0
+
+
+def test_straight_aorta_workload_is_the_papers_case():
+    # the convergence workload is built on the paper's printed case: 25 diameters,
+    # Womersley number 16 at every printed resolution (diffusive scaling keeps it)
+    import math
+
+    import golden_fixtures
+    from paper_2112_05258_gb300 import e5_study
+    from workloads import axisym as wa
+    from workloads.configs import viscosity
+    ex = golden_fixtures.load("straight_aorta_section3_1_3.txt")
+    printed = tuple(ex[f"n_d_{k}"] for k in range(1, 6))
+    assert tuple(e5_study.RESOLUTIONS) == printed
+    for n_d in printed[:3]:
+        inst = wa.straight_aorta(n_d)
+        nr, nx = inst.node.shape
+        assert nx - 2 == round(ex["length_D"] * n_d)          # lattice length in diameters
+        T = wa.e5_period(n_d)
+        alpha = (n_d / 2.0) * math.sqrt(2 * math.pi / T / viscosity(inst.tau))
+        assert alpha == pytest.approx(ex["womersley"], rel=1e-12)
