@@ -283,3 +283,51 @@ def test_wall_shear_tube_direction_and_balance():
     perimeter = 2 * np.pi * R
     mean_wss = g * (node == 0).sum() / perimeter      # force balance per unit length
     assert w[at, 2].mean() == pytest.approx(mean_wss, rel=0.25)
+
+
+def test_nee_copies_the_neighbours_non_equilibrium():
+    # Eq. Non-equilibrium3 with a pressure-type 0D node and x_f out of
+    # equilibrium: the population entering x_f from the node is
+    # f*_i(x_f) + f^eq_i(P*, v(x_f)) - f^eq_i(P(x_f), v(x_f)), i.e. the
+    # neighbour's post-collision population shifted by w_i (P* - P(x_f)) / c_s^2.
+    # f^eq (Eq. feq, rho0 = 1) and the BGK step are restated here.
+    ex = np.array([0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0])
+    ey = np.array([0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1])
+    ez = np.array([0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1])
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+
+    def feq(P, v):
+        eu = ex * v[0] + ey * v[1] + ez * v[2]
+        return w * (P / CS2 + 3 * eu + 4.5 * eu * eu - 1.5 * (v @ v))
+
+    tau, p_in, p_out = 0.8, 3e-3, -2e-3
+    inst = configs.pressure_tube(12, 12, 10, 4.0, tau, p_in, p_out)
+    f0 = configs.random_populations(inst, seed=11, amp=2e-2)
+    o = oracle.Oracle(inst)
+    o.set_populations(f0)
+    o.step(1)
+    f1 = o.populations()
+    nx, ny, nz = inst.shape
+    node = inst.node
+    checked = 0
+    for z_f, z_b, code, p0d, dirs in ((1, 0, 2, p_in, np.flatnonzero(ez == 1)),
+                                       (nz - 2, nz - 1, 3, p_out, np.flatnonzero(ez == -1))):
+        for y in range(ny):
+            for x in range(nx):
+                if node[z_f, y, x] != 0:
+                    continue
+                c = x + nx * (y + ny * z_f)
+                f = f0[:, c]
+                P = CS2 * f.sum()
+                v = np.array([ex @ f, ey @ f, ez @ f])
+                fstar = f - (f - feq(P, v)) / tau
+                for i in dirs:
+                    xb, yb = x - ex[i], y - ey[i]
+                    if not (0 <= xb < nx and 0 <= yb < ny) or node[z_b, yb, xb] != code:
+                        continue
+                    want = fstar[i] + feq(CS2 + p0d, v)[i] - feq(P, v)[i]
+                    assert f1[i, c] == pytest.approx(want, rel=1e-13, abs=1e-16)
+                    # the pressure form of the same identity
+                    assert want == pytest.approx(fstar[i] + w[i] * (CS2 + p0d - P) / CS2, rel=1e-13)
+                    checked += 1
+    assert checked == o.n_links(0) + o.n_links(1) > 0
