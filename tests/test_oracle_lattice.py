@@ -331,3 +331,38 @@ def test_nee_copies_the_neighbours_non_equilibrium():
                     assert want == pytest.approx(fstar[i] + w[i] * (CS2 + p0d - P) / CS2, rel=1e-13)
                     checked += 1
     assert checked == o.n_links(0) + o.n_links(1) > 0
+
+
+def test_velocity_inlet_prescribes_the_next_steps_value():
+    # Algorithm 1 sets the 0D value of t_{n+1} before the coupling of that
+    # step: from rest (x_f at equilibrium), the population entering x_f from
+    # an inlet node after step 0 -> 1 is f^eq_i(P(x_f), v*(t_1)) with
+    # v* = u_mean + Re{c e^{i omega t}} of that node (Eq. Non-equilibrium3,
+    # velocity type), here along +z.  f^eq (Eq. feq, rho0 = 1) is restated.
+    ex = np.array([0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0])
+    ey = np.array([0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1])
+    ez = np.array([0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1])
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    inst = configs.rigid_tube(12, 12, 10, radius=4.0, period=40)   # a short beat: v* moves fast
+    omega = inst.boundaries[0].params[0]
+    prof = inst.boundaries[0].profile
+    nx, ny, nz = inst.shape
+    nodes = inst.boundary_nodes(0)
+    o = oracle.Oracle(inst)
+    o.set_populations(np.repeat(w[:, None], o.N, axis=1))   # rest: P = c_s^2, v = 0
+    o.step(1)
+    f1 = o.populations()
+    checked = 0
+    for q, b in enumerate(nodes):
+        xb, yb = b % nx, (b // nx) % ny
+        vz = prof[q, 0] + prof[q, 1] * np.cos(omega * 1.0) - prof[q, 2] * np.sin(omega * 1.0)
+        for i in np.flatnonzero(ez == 1):
+            x, y = xb + ex[i], yb + ey[i]
+            if not (0 <= x < nx and 0 <= y < ny) or inst.node[1, y, x] != 0:
+                continue
+            want = w[i] * (1.0 + 3 * vz + 4.5 * vz * vz - 1.5 * vz * vz)
+            assert f1[i, x + nx * (y + ny * 1)] == pytest.approx(want, rel=1e-13)
+            checked += 1
+    assert checked == o.n_links(0) > 0
+    # the value of t_0 would differ by far more than the tolerance
+    assert abs(np.cos(omega) - 1.0) > 1e-3
