@@ -366,3 +366,58 @@ def test_velocity_inlet_prescribes_the_next_steps_value():
     assert checked == o.n_links(0) > 0
     # the value of t_0 would differ by far more than the tolerance
     assert abs(np.cos(omega) - 1.0) > 1e-3
+
+
+def test_nee_carries_the_neighbours_forcing():
+    # Eq. Non-equilibrium3 rests on f*_i(x_f) = f^eq_i + (1 - 1/tau) f^neq_i + F_i:
+    # with a force density b at x_f the entering population is the neighbour's
+    # forced post-collision value, shifted by f^eq_i(P*, v) - f^eq_i(P(x_f), v),
+    # v = j + b/2 (Eq. v).  f^eq (Eq. feq), Guo's F_i (Eq. f) and the BGK step
+    # are restated here.
+    ex = np.array([0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0])
+    ey = np.array([0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1])
+    ez = np.array([0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1])
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    E = np.stack([ex, ey, ez], axis=1).astype(float)
+
+    def feq(P, v):
+        eu = E @ v
+        return w * (P / CS2 + 3 * eu + 4.5 * eu * eu - 1.5 * (v @ v))
+
+    def guo(tau, v, b):
+        eu, eb = E @ v, E @ b
+        return (1 - 0.5 / tau) * w * (3 * (eb - v @ b) + 9 * eu * eb)
+
+    tau, p_in, p_out = 0.8, 3e-3, -2e-3
+    g = np.array([2e-4, -1e-4, 3e-4])
+    inst = configs.pressure_tube(12, 12, 10, 4.0, tau, p_in, p_out)
+    f0 = configs.random_populations(inst, seed=5, amp=1e-2)
+    o = oracle.Oracle(inst)
+    o.set_populations(f0)
+    o.set_body_force(list(g))
+    o.step(1)
+    f1 = o.populations()
+    nx, ny, nz = inst.shape
+    node = inst.node
+    checked, shift = 0, 0.0
+    for z_f, z_b, code, p0d, dirs in ((1, 0, 2, p_in, np.flatnonzero(ez == 1)),
+                                       (nz - 2, nz - 1, 3, p_out, np.flatnonzero(ez == -1))):
+        for y in range(ny):
+            for x in range(nx):
+                if node[z_f, y, x] != 0:
+                    continue
+                c = x + nx * (y + ny * z_f)
+                f = f0[:, c]
+                P = CS2 * f.sum()
+                v = E.T @ f + g / 2
+                fstar = f - (f - feq(P, v)) / tau + guo(tau, v, g)
+                for i in dirs:
+                    xb, yb = x - ex[i], y - ey[i]
+                    if not (0 <= xb < nx and 0 <= yb < ny) or node[z_b, yb, xb] != code:
+                        continue
+                    want = fstar[i] + feq(CS2 + p0d, v)[i] - feq(P, v)[i]
+                    assert f1[i, c] == pytest.approx(want, rel=1e-13, abs=1e-16)
+                    shift = max(shift, abs(guo(tau, v, g)[i]))
+                    checked += 1
+    assert checked == o.n_links(0) + o.n_links(1) > 0
+    assert shift > 1e-6   # the forcing term is far above the tolerance
