@@ -148,3 +148,29 @@ def test_membrane_motion_stays_bounded():
         dr = np.hypot(*(X[:, :2] - c).T) - r0
         assert abs(dr.mean()) < 0.03
         assert np.percentile(np.linalg.norm(X - inst.ib.X0, axis=1), 99) < 0.2
+
+
+def test_interpolated_velocity_includes_half_the_force_density():
+    # the IB interpolates the fluid velocity of Eq. v, j/rho0 + b/(2 rho0), of
+    # f(t_n) with the force density b still held from the previous step: in a
+    # periodic box under a uniform body force g and with the penalty off, b is
+    # g after the first step, so the second step's V_f is j(t_1) + g/2 for
+    # every node (partition of unity; j summed here from f(t_1))
+    rng = np.random.default_rng(3)
+    X0 = rng.uniform(4, 8, (6, 3))
+    inst, o = _box_with_nodes(X0)
+    u0 = np.array([0.01, -0.02, 0.005])
+    g = np.array([3e-4, -2e-4, 5e-4])
+    _fill_velocity(o, inst, lambda p: u0)
+    o.set_body_force(list(g))
+    o.step(1)
+    f1 = o.populations()
+    ex = np.array([0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0])
+    ey = np.array([0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1])
+    ez = np.array([0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1])
+    j1 = np.stack([ex @ f1, ey @ f1, ez @ f1], axis=1)
+    assert np.abs(j1 - j1[0]).max() < 1e-15                 # uniform field
+    o.step(1)
+    Vf = o.ib_state()[3]
+    assert np.allclose(Vf, j1[0] + g / 2, rtol=0, atol=1e-15), (Vf[0], j1[0], g)
+    assert np.abs(g / 2).min() > 1e-5                        # far above the tolerance
