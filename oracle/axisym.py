@@ -29,6 +29,9 @@ must recover, with rho0 = 1):
   the source;
 * the axis is a mirror: a population that would come from below r = 0 is
   the mirrored population (e_r -> -e_r) of the node above it;
+  Parity partly unpinned: the convective terms -u_x u_r / r and -u_r^2 / r
+  vanish in every closed-form case these boundaries admit (no radial
+  velocity), so only the derivation and the GPU agreement back them;
 * rigid walls: halfway bounce-back; 0D boundaries: Eq. Non-equilibrium3 per
   link with the same source terms at x_f as the collision there; boundary
   flow Q = sum over the first fluid layer of 2 pi r n.j / sum f (area 2 pi r
