@@ -421,3 +421,67 @@ def test_nee_carries_the_neighbours_forcing():
                     checked += 1
     assert checked == o.n_links(0) + o.n_links(1) > 0
     assert shift > 1e-6   # the forcing term is far above the tolerance
+
+
+def test_closed_valve_velocity_is_smoothed_at_the_next_steps_time():
+    # after the aortic valve closes in the step from t_n (T_d = t_n), the inlet
+    # links prescribe v* = v_0(T_d) S(t_{m+1}, T_d, N_S) in every later step m
+    # (Eqs. SmoothFunction, vnew; the 0D value of t_{m+1} as Algorithm 1 orders
+    # it), with v_0 the closure-step velocity of each link's x_f and P* = P(x_f):
+    # the entering population is f^eq(P(x_f), v*) + (1 - 1/tau) f^neq(x_f).
+    # f^eq (Eq. feq) and S (Eq. SmoothFunction) are restated here.
+    ex = np.array([0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0])
+    ey = np.array([0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1])
+    ez = np.array([0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1])
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    E = np.stack([ex, ey, ez], axis=1).astype(float)
+
+    def feq(P, v):
+        eu = E @ v
+        return w * (P / CS2 + 3 * eu + 4.5 * eu * eu - 1.5 * (v @ v))
+
+    def S(t, t0, L):
+        if t <= t0:
+            return 1.0
+        if t >= t0 + L:
+            return 0.0
+        u = (t - t0) / L
+        return float(np.exp(2.0 * np.exp(-1.0 / u) / (u - 1.0)))
+
+    inst = configs.lv_tube(period=300)
+    tau, n_s = inst.tau, inst.boundaries[0].params[2]
+    nx, ny, nz = inst.shape
+    o = oracle.Oracle(inst)
+    links = []
+    for y in range(ny):
+        for x in range(nx):
+            if inst.node[1, y, x] != 0:
+                continue
+            for i in np.flatnonzero(ez == 1):
+                xb, yb = x - ex[i], y - ey[i]
+                if 0 <= xb < nx and 0 <= yb < ny and inst.node[0, yb, xb] == 2:
+                    links.append((x + nx * (y + ny * 1), i))
+    assert len(links) == o.n_links(0)
+    was_open, Td, v0, checked = 0.0, None, {}, 0
+    for n in range(1200):
+        f = o.populations()
+        o.step(1)
+        st = o.state_0d(0)
+        if Td is None and was_open == 1.0 and st[6] == 0.0:
+            Td = n
+            assert st[7] == pytest.approx(Td)
+            v0 = {c: E.T @ f[:, c] for c, _ in links}           # no force here: v = j
+        was_open = st[6]
+        if Td is not None and n in (Td, Td + 1, Td + n_s // 2) and st[6] == 0.0:
+            f1 = o.populations()
+            s = S(n + 1.0, Td, n_s)
+            for c, i in links:
+                P, v = CS2 * f[:, c].sum(), E.T @ f[:, c]
+                want = feq(P, v0[c] * s)[i] + (1 - 1 / tau) * (f[i, c] - feq(P, v)[i])
+                assert f1[i, c] == pytest.approx(want, rel=1e-12, abs=1e-15), (n, Td, i)
+                checked += 1
+            if n == Td + n_s // 2:
+                break
+    assert Td is not None and checked == 3 * len(links)
+    # one step earlier the smoothing factor differs far beyond the tolerance
+    assert abs(S(Td + n_s / 2 + 1, Td, n_s) - S(Td + n_s / 2, Td, n_s)) > 1e-3
