@@ -925,7 +925,9 @@ void orc_get_0d(void *h, int k, double *out)
  * the wall normal n is the normalised sum of e_i over the directions whose
  * pull source is a wall (pointing into the fluid); the output is the
  * tangential traction sigma.n - (n.sigma.n) n, 3 values per box cell, zero
- * away from walls.  The force density b is the one of the last step. */
+ * away from walls.  The force density b is the one of the last step.
+ * Parity partly unpinned: the (v b + b v)/2 term has no tangential part in
+ * the force-driven channel and tube pins, so only the reading backs it. */
 void orc_wall_shear(void *h, double *out)
 {
     orc_t *o = (orc_t *)h;
