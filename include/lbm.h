@@ -183,7 +183,9 @@ lbm_status lbm_init_populations(lbm_handle *h, int inst, const double *f);
 lbm_status lbm_step(lbm_handle *h, int64_t n);
 
 /* Waits for the stream; returns LBM_ERR_UNSTABLE if the device status word
- * recorded NaN/Inf or |v| > 0.3 since creation. */
+ * recorded NaN/Inf or |v| > 0.3 (stream-collide) or a wall node more than one
+ * cell from its reference cell, i.e. outside its immersed-boundary support
+ * box (node kernel), since creation.  The state stays readable. */
 lbm_status lbm_sync(lbm_handle *h);
 
 /* Host outputs, box order, nx*ny*nz doubles each (non-fluid nodes 0):
@@ -315,8 +317,15 @@ lbm_status lbm_get_kernel_time(lbm_handle *h, int64_t *launches, double *total_m
 lbm_status lbm_boundary_flux_noalloc(const double *P, const double *j_normal, const int32_t *cells,
                                      int64_t n_cells, double *out, void *stream);
 
+/* Sizes and counters of the handle (host output *info; see lbm_info_t).
+ * LBM_ERR_ARG for a NULL argument; no device work. */
 lbm_status lbm_get_info(lbm_handle *h, lbm_info_t *info);
+/* Text of the handle's most recent failure (empty if none); owned by the
+ * handle, valid until its next call or lbm_destroy.  NULL h gives a static
+ * message. */
 const char *lbm_last_error(const lbm_handle *h);
+/* Waits for the handle's stream, frees all its device and page-locked host
+ * memory and CUDA graphs; NULL is ignored. */
 void lbm_destroy(lbm_handle *h);
 
 #ifdef __cplusplus
