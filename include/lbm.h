@@ -309,7 +309,12 @@ lbm_status lbm_get_kernel_time(lbm_handle *h, int64_t *launches, double *total_m
  * a fixed 64 KiB device array that every GPU which loads the library holds
  * until the process exits.  The first call on a device looks up that array's
  * device address (cudaGetSymbolAddress) with the device current, so make the
- * first call on each device before any stream capture.  All calls share the
+ * first call on each device before any stream capture.  That address is kept
+ * for the life of the process: after cudaDeviceReset, or anything else that
+ * destroys the device's primary context, it is stale, so do not call this
+ * function on that device again in the same process.  A CUDA error already
+ * pending when the call starts is returned as LBM_ERR_CUDA (message on
+ * stderr) before anything is launched, and left pending.  All calls share the
  * array: each call overwrites every partial it reads, so no clearing is
  * needed, but calls that overlap on the GPU (different streams, or
  * concurrent host threads) race on it and must be serialised by the caller.

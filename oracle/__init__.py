@@ -298,3 +298,6 @@ class Oracle:
 
     def n_links(self, k: int) -> int:
         return lib().orc_n_links(self._h, int(k))
+
+
+from .periodic import cycle_change  # noqa: E402,F401  (periodic-state criterion)

@@ -461,12 +461,23 @@ int orc_set_filaments(void *h, long n_fil, const long *start, const long *count,
     return 0;
 }
 
+/* A uniform body force g (tests only).  It is also, from now until the next
+ * step replaces it, the force density b held at every fluid node, so that a
+ * read-out taken before the first step (the wall shear stress) sees the b
+ * that the step producing the current populations would have used; any
+ * immersed-boundary contribution is re-spread by the next step. */
 void orc_set_body_force(void *h, double gx, double gy, double gz)
 {
     orc_t *o = (orc_t *)h;
     o->g[0] = gx;
     o->g[1] = gy;
     o->g[2] = gz;
+    for (long c = 0; c < o->N; c++) {
+        int fl = o->node[c] == N_FLUID;
+        o->bx[c] = fl ? gx : 0.0;
+        o->by[c] = fl ? gy : 0.0;
+        o->bz[c] = fl ? gz : 0.0;
+    }
 }
 
 void orc_set_populations(void *h, const double *f)
@@ -926,8 +937,9 @@ void orc_get_0d(void *h, int k, double *out)
  * pull source is a wall (pointing into the fluid); the output is the
  * tangential traction sigma.n - (n.sigma.n) n, 3 values per box cell, zero
  * away from walls.  The force density b is the one of the last step.
- * Parity partly unpinned: the (v b + b v)/2 term has no tangential part in
- * the force-driven channel and tube pins, so only the reading backs it. */
+ * The (v b + b v)/2 term is what makes a uniformly accelerated fluid (no
+ * velocity gradient) carry no stress: its non-equilibrium second moment is
+ * exactly -(v b + b v)/2 under the BGK update with Guo forcing (pinned). */
 void orc_wall_shear(void *h, double *out)
 {
     orc_t *o = (orc_t *)h;

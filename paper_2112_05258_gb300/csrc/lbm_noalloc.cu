@@ -87,8 +87,16 @@ extern "C" lbm_status lbm_boundary_flux_noalloc(const double *P, const double *j
                 (long long)n_cells, (long long)NA_CHUNK * NA_MAX_CHUNKS, NA_MAX_CHUNKS);
         return LBM_ERR_ARG;
     }
+    // an error left by earlier, unrelated work is reported as such (and left
+    // pending for the caller), not mistaken for a failure of this call's launches
+    cudaError_t e = cudaPeekAtLastError();
+    if (e != cudaSuccess) {
+        fprintf(stderr, "lbm_boundary_flux_noalloc: an earlier CUDA error is pending (%s); nothing launched\n",
+                cudaGetErrorString(e));
+        return LBM_ERR_CUDA;
+    }
     int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
+    e = cudaGetDevice(&dev);
     if (e != cudaSuccess || dev < 0 || dev >= NA_MAX_DEVICES) {
         fprintf(stderr, "lbm_boundary_flux_noalloc: no usable current device (%s)\n", cudaGetErrorString(e));
         return LBM_ERR_CUDA;
@@ -96,7 +104,9 @@ extern "C" lbm_status lbm_boundary_flux_noalloc(const double *P, const double *j
     double *scratch = nullptr;
     {
         // once per device, with that device current: the device address of the
-        // static scratch array (its name is only a host-side stand-in)
+        // static scratch array (its name is only a host-side stand-in).  The
+        // address is kept for the life of the process; a device reset or a new
+        // primary context on that device makes it stale.
         std::lock_guard<std::mutex> lock(g_mu);
         if (!g_scratch_addr[dev]) {
             void *ptr = nullptr;

@@ -285,6 +285,40 @@ def test_wall_shear_tube_direction_and_balance():
     assert w[at, 2].mean() == pytest.approx(mean_wss, rel=0.25)
 
 
+def test_wall_shear_of_uniformly_accelerated_fluid_is_zero():
+    # A uniform fluid under a uniform force b accelerates without velocity
+    # gradients, so it carries no viscous stress.  Under the BGK update with
+    # Guo forcing the non-equilibrium second moment of such a state tends to
+    # -(v b + b v)/2 exactly (the recursion Pi_{n+1} = (1 - 1/tau) Pi_n
+    # - (v_n b + b v_n)/(2 tau) - b b with v_{n+1} = v_n + b has that particular
+    # solution; the start-up decays as (1 - 1/tau)^n), which the (v b + b v)/2
+    # term of the stress cancels.  The state is made by the oracle on a fully
+    # periodic box, then read out next to the walls of a channel (the wall
+    # normal only picks the traction's direction); b has a wall-normal part
+    # and v a tangential one, so the term has a tangential traction
+    # (1 - 1/(2 tau)) (v_t b_n) / 2 that the read-out must cancel.
+    nx, ny, nz, tau = 4, 7, 5, 0.8
+    g = np.array([4e-5, 1e-4, -3e-5])
+    v0 = np.array([0.03, 0.0, 0.01])
+    box = oracle.Oracle(Instance(node=np.zeros((nz, ny, nx), np.uint8), tau=tau), periodic=7)
+    box.set_body_force(g)
+    box.set_populations(np.repeat(oracle.feq(CS2, v0)[:, None], nx * ny * nz, axis=1))
+    box.step(80)
+    f = box.populations()
+    assert np.abs(f - f[:, :1]).max() == 0.0                 # still uniform
+    node = geometry.plates_channel(nx, ny, nz)                 # walls at y = 0 and y = ny - 1
+    ch = oracle.Oracle(Instance(node=node, tau=tau), periodic=1 | 4)
+    ch.set_populations(f)
+    ch.set_body_force(g)
+    w = ch.wall_shear().reshape(nz, ny, nx, 3)
+    v = box.macros()[1:]
+    vx, vz = v[0][0] + g[0] / 2, v[2][0] + g[2] / 2
+    term = (1 - 1 / (2 * tau)) * 0.5 * np.array([vx * g[1], vz * g[1]])   # what a missing term leaves
+    assert np.abs(term).min() > 1e-7
+    assert np.abs(w[:, [1, ny - 2]]).max() < 1e-9 * np.abs(term).max()
+    assert np.abs(w[:, 2:ny - 2]).max() == 0.0
+
+
 def test_nee_copies_the_neighbours_non_equilibrium():
     # Eq. Non-equilibrium3 with a pressure-type 0D node and x_f out of
     # equilibrium: the population entering x_f from the node is
