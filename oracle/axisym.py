@@ -25,13 +25,16 @@ must recover, with rho0 = 1):
   applied through the Guo forcing term (with any body force added); the
   strain rates are taken locally from the non-equilibrium stress,
   nu (d_a u_b + d_b u_a) = -(1 - 1/(2 tau)) Pi^neq_ab,
-  Pi^neq = sum_i e_i e_i (f_i - f^eq_i(P, j)), and u = j (unforced) inside
-  the source;
+  Pi^neq = sum_i e_i e_i (f_i - f^eq_i(c_s^2 sum f, j)) (against the
+  equilibrium of f's own moments: the Chapman-Enskog expansion of this
+  scheme gives sum e e f^(1) = -tau c_s^2 (grad v + grad v^T)
+  - (c_s^2 / 2) m I - (v g + g v) / 2, and the last two terms are exactly
+  what f^eq(c_s^2 sum f, j) differs from f^eq(P, v) by, to first order),
+  and u = j (unforced) inside the source;
 * the axis is a mirror: a population that would come from below r = 0 is
   the mirrored population (e_r -> -e_r) of the node above it;
-  Parity partly unpinned: the convective terms -u_x u_r / r and -u_r^2 / r
-  vanish in every closed-form case these boundaries admit (no radial
-  velocity), so only the derivation and the GPU agreement back them;
+  flows with radial velocity (every source term active) are pinned by a
+  manufactured steady solution in a periodic pipe (tests);
 * rigid walls: halfway bounce-back; 0D boundaries: Eq. Non-equilibrium3 per
   link with the same source terms at x_f as the collision there; boundary
   flow Q = sum over the first fluid layer of 2 pi r n.j / sum f (area 2 pi r
@@ -76,7 +79,9 @@ def guo(tau, ux, ur, gx, gr):
 class AxiOracle:
     """One axisymmetric instance.  ``node``: (nr, nx) uint8 codes; ``bcs``:
     :class:`workloads.spec.Boundary` objects with axis 0; ``periodic_x`` and
-    ``body_force`` (axial, per unit volume) are for the pins."""
+    ``body_force`` are for the pins: a scalar is a uniform axial force per
+    unit volume, a pair of (nr, nx) arrays a force field (g_x, g_r) given
+    per node, added to the axisymmetric source like the scalar."""
 
     def __init__(self, node, tau, bcs=(), q_scale=1, periodic_x=False, body_force=0.0):
         self.node = np.asarray(node, dtype=np.uint8)
@@ -85,7 +90,12 @@ class AxiOracle:
         self.nu = CS2 * (self.tau - 0.5)
         self.q_scale = int(q_scale)
         self.periodic_x = bool(periodic_x)
-        self.G = float(body_force)
+        if np.ndim(body_force) == 0:
+            self.Gx, self.Gr = float(body_force), 0.0
+        else:
+            gx, gr = body_force
+            self.Gx = np.array(gx, dtype=np.float64).reshape(self.nr, self.nx)
+            self.Gr = np.array(gr, dtype=np.float64).reshape(self.nr, self.nx)
         self.r = (np.arange(self.nr) + 0.5)[:, None] * np.ones((1, self.nx))
         self.fluid = self.node == 0
         self.f = np.where(self.node != 1, 1.0, 0.0)[None] * W[:, None, None]
@@ -167,13 +177,18 @@ class AxiOracle:
         r = self.r
         m = -jr / r                                          # mass source (h^(1))
         P = CS2 * (sf + 0.5 * m)
-        fe = feq(P, jx, jr)
+        # the strain rates are read from f against the equilibrium of its own
+        # moments (c_s^2 sum f, j): the first-order non-equilibrium stress
+        # then equals -tau c_s^2 (grad v + grad v^T) alone, without the
+        # isotropic -(c_s^2 / 2) m I of the mass source's half step (which a
+        # comparison with f^eq(P, j) would leave on the diagonal)
+        fe = feq(CS2 * sf, jx, jr)
         dn = f - fe
         pxr = np.tensordot(EX * ER, dn, axes=1)
         prr = np.tensordot(ER * ER, dn, axes=1)
         k = 1.0 - 0.5 / self.tau
-        gx = -k * pxr / r - jx * jr / r + self.G
-        gr = -k * prr / r - 2.0 * self.nu * jr / (r * r) - jr * jr / r
+        gx = -k * pxr / r - jx * jr / r + self.Gx
+        gr = -k * prr / r - 2.0 * self.nu * jr / (r * r) - jr * jr / r + self.Gr
         z = ~self.fluid
         for a in (sf, jx, jr, m, P, gx, gr):
             a[z] = 0.0

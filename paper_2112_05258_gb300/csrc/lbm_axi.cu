@@ -17,8 +17,10 @@
 //   m   = -j_r / r,                 P = c_s^2 (sum f + m/2)
 //   g_x = -(1 - 1/(2 tau)) Pi_xr / r - j_x j_r / r
 //   g_r = -(1 - 1/(2 tau)) Pi_rr / r - 2 nu j_r / r^2 - j_r^2 / r
-// where Pi = sum e e (f - f^eq(P, j)) is the non-equilibrium stress; v = j +
-// g/2; the collision adds the Guo term of g and (1 - 1/(2 tau)) w_i m.
+// where Pi = sum e e (f - f^eq(c_s^2 sum f, j)) is the non-equilibrium stress
+// against the equilibrium of f's own moments (so that the isotropic part the
+// mass source leaves in f's second moment does not enter the strain rate);
+// v = j + g/2; the collision adds the Guo term of g and (1 - 1/(2 tau)) w_i m.
 // Populations are stored as deviations s = f - w (FP32 or FP64), in SoA
 // order f[i][j nx + x]; the resident state is f*(t_n) with the ghosts of
 // t_{n+1} in the 0D boundary nodes' slots, as in the 3D lattice.
@@ -136,9 +138,10 @@ __global__ void __launch_bounds__(256) k_axi_collide(const S *__restrict__ fin, 
     Consts<R>::get(p, j, &omega, &k, &nu, &inv_r);
     const R m = -jr * inv_r;
     const R sp = sd + R(0.5) * m;                       // 3P - 1
-    // non-equilibrium stress of f against f^eq(P, j): Pi^eq_xr = j_x j_r, Pi^eq_rr = P + j_r^2
+    // non-equilibrium stress of f against f^eq(c_s^2 sum f, j): Pi^eq_xr = j_x j_r,
+    // Pi^eq_rr = c_s^2 sum f + j_r^2 (sum f = 1 + sd)
     const R Pi_xr = pxr - jx * jr;
-    const R Pi_rr = prr - sp / R(3) - jr * jr;
+    const R Pi_rr = prr - sd / R(3) - jr * jr;
     const R gx = -k * Pi_xr * inv_r - jx * jr * inv_r;
     const R gr = -k * Pi_rr * inv_r - R(2) * nu * jr * inv_r * inv_r - jr * jr * inv_r;
     const R vx = jx + R(0.5) * gx, vr = jr + R(0.5) * gr;
@@ -196,7 +199,7 @@ __global__ void k_axi_gather(const S *__restrict__ fin, Params p, double *f9, do
     const double tau = p.tau, k = 1.0 - 0.5 / tau, nu = (tau - 0.5) / 3.0, inv_r = 1.0 / (j + 0.5);
     const double m = -jr * inv_r, sp = sd + 0.5 * m;
     const double gx = -k * (pxr - jx * jr) * inv_r - jx * jr * inv_r;
-    const double gr = -k * (prr - sp / 3.0 - jr * jr) * inv_r - 2.0 * nu * jr * inv_r * inv_r - jr * jr * inv_r;
+    const double gr = -k * (prr - sd / 3.0 - jr * jr) * inv_r - 2.0 * nu * jr * inv_r * inv_r - jr * jr * inv_r;
     mac3[c] = (1.0 + sp) / 3.0;
     mac3[n + c] = jx + 0.5 * gx;
     mac3[2 * n + c] = jr + 0.5 * gr;

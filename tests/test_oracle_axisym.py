@@ -58,10 +58,10 @@ def test_womersley_second_order():
         U = G0 / (1j * w) * (1 - special.jv(0, i32 * alpha * r / R) / special.jv(0, i32 * alpha))
         err = mx = 0.0
         for n in range(int(5 * T)):
-            o.G = G0 * np.cos(w * n)
+            o.Gx = G0 * np.cos(w * n)
             o.step(1)
             if n > 4 * T:
-                o.G = G0 * np.cos(w * (n + 1))
+                o.Gx = G0 * np.cos(w * (n + 1))
                 ua = (U * np.exp(1j * w * (n + 1))).real
                 err = max(err, np.abs(o.fields()[1][:, 0] - ua).max())
                 mx = max(mx, np.abs(ua).max())
@@ -128,3 +128,61 @@ def test_straight_aorta_workload_is_the_papers_case():
         T = wa.e5_period(n_d)
         alpha = (n_d / 2.0) * math.sqrt(2 * math.pi / T / viscosity(inst.tau))
         assert alpha == pytest.approx(ex["womersley"], rel=1e-12)
+
+
+def _mms_fields(x, r, R, A, k):
+    """Manufactured axisymmetric flow from the Stokes stream function
+    psi = A r^2 (1 - r^2/R^2)^2 sin(k x): u_x = psi_r / r, u_r = -psi_x / r.
+    It is divergence-free in the axisymmetric sense, vanishes on the wall
+    r = R, and is regular on the axis (u_r ~ r, d_r u_x = 0)."""
+    s = (r / R) ** 2
+    ux = 2 * A * np.sin(k * x) * (1 - s) * (1 - 3 * s)
+    ur = -A * k * r * (1 - s) ** 2 * np.cos(k * x)
+    return ux, ur
+
+
+def _mms_force(x, r, R, A, k, nu, h=1e-4):
+    """Body force that makes the manufactured flow a steady solution of the
+    axisymmetric incompressible Navier-Stokes equations with constant
+    pressure: g = (u.grad) u - nu lap u, lap of the radial component with
+    the -u_r / r^2 term; derivatives by central differences of the closed
+    form (step h, error ~h^2)."""
+    f = lambda a, b: _mms_fields(a, b, R, A, k)
+    u = f(x, r)
+    xp, xm, rp, rm = f(x + h, r), f(x - h, r), f(x, r + h), f(x, r - h)
+    g = []
+    for c in range(2):
+        dx = (xp[c] - xm[c]) / (2 * h)
+        dr = (rp[c] - rm[c]) / (2 * h)
+        lap = (xp[c] - 2 * u[c] + xm[c]) / h ** 2 + (rp[c] - 2 * u[c] + rm[c]) / h ** 2 + dr / r
+        if c == 1:
+            lap -= u[1] / r ** 2
+        g.append(u[0] * dx + u[1] * dr - nu * lap)
+    return g
+
+
+def _mms_error(R, tau=0.8):
+    nu = (tau - 0.5) / 3
+    nx = 4 * R
+    k = 2 * np.pi / nx
+    A = 0.16 / R                      # fixed Reynolds number 2 A R / nu = 3.2 under refinement
+    x = np.arange(nx)[None, :] * np.ones((R, 1))
+    r = (np.arange(R) + 0.5)[:, None] * np.ones((1, nx))
+    o = ax.AxiOracle(np.zeros((R, nx), np.uint8), tau, periodic_x=True, body_force=_mms_force(x, r, R, A, k, nu))
+    ux, ur = _mms_fields(x, r, R, A, k)
+    o.set_populations(ax.feq(ax.CS2 + 0 * ux, ux, ur))
+    o.step(int(8 * R * R / nu))       # eight viscous times: steady to far below the error
+    _, vx, vr = o.fields()
+    um = np.abs(ux).max()
+    assert np.abs(ur).max() > 0.2 * um      # a flow with real radial velocity
+    return np.abs(vx - ux).max() / um, np.abs(vr - ur).max() / um
+
+
+def test_manufactured_radial_flow_converges():
+    # every source term is active: mass -u_r/r, the viscous terms with d_x u_r
+    # and d_r u_r, and the convective -u_x u_r / r and -u_r^2 / r (Reynolds
+    # number 3.2, so leaving either out moves the steady flow by percents)
+    e8 = _mms_error(8)
+    e16 = _mms_error(16)
+    assert e16[0] < 8e-3 and e16[1] < 1.5e-3, (e8, e16)
+    assert e8[0] / e16[0] > 3.0 and e8[1] / e16[1] > 2.5, (e8, e16)
