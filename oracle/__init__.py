@@ -32,12 +32,18 @@ _u8p = ctypes.POINTER(ctypes.c_uint8)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with plain gcc (IEEE FP64, no fast-math, no FMA contraction)."""
+    """Compile the oracle with plain gcc (IEEE FP64, no fast-math, no FMA
+    contraction), with OpenMP for the per-cell loops where gcc has it (the
+    results do not depend on the thread count; one thread by default)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
-                               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
+                "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _SO)
     return _SO
 
@@ -99,6 +105,8 @@ def lib():
             L.orc_lv_ode_ord.argtypes = [ctypes.c_double] * 6 + [ctypes.c_int]
             L.orc_phi.restype = ctypes.c_double
             L.orc_phi.argtypes = [ctypes.c_double]
+            L.orc_set_threads.argtypes = [ctypes.c_int]
+            L.orc_openmp.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -181,6 +189,15 @@ def filament_force(X, gl, gr, ds: float, Eh: float, EI: float) -> np.ndarray:
 
 def phi(r: float) -> float:
     return lib().orc_phi(r)
+
+
+def set_threads(n: int) -> int:
+    """Threads of the oracle's per-cell loops (process-wide); returns the
+    count in effect (1 when the oracle was built without OpenMP)."""
+    L = lib()
+    n = max(1, int(n)) if L.orc_openmp() else 1
+    L.orc_set_threads(n)
+    return n
 
 
 # ---- the lattice ---------------------------------------------------------

@@ -18,6 +18,14 @@
  * No loop is fused, blocked or reordered.  Streaming is written in the
  * paper's push form f_i(x + e_i, t + 1) = f*_i(x).
  *
+ * Threads: the loops over cells whose iterations write only their own
+ * cell's values (macros, force-density reset, forced velocity, collision,
+ * streaming) may be spread over orc_set_threads(n) OpenMP threads when the
+ * file is compiled with -fopenmp; every reduction, the immersed-boundary
+ * spreading and the 0D models stay serial in their fixed order, so the
+ * results are the same bits for any thread count.  The default is one
+ * thread.
+ *
  * Readings of the paper taken where it is silent or ambiguous are stated at
  * the function they affect.
  */
@@ -28,6 +36,24 @@
 
 #define NQ 19
 #define MAXBC 8
+
+/* threads of the per-cell loops (see the header comment) */
+static int g_threads = 1;
+#ifdef _OPENMP
+#define ORC_PAR_CELLS _Pragma("omp parallel for schedule(static) num_threads(g_threads)")
+#else
+#define ORC_PAR_CELLS
+#endif
+
+void orc_set_threads(int n) { g_threads = n < 1 ? 1 : n; }
+int orc_openmp(void)
+{
+#ifdef _OPENMP
+    return 1;
+#else
+    return 0;
+#endif
+}
 
 /* D3Q19 velocity set: rest, 6 face neighbours, 12 edge neighbours
  * (Section 2.1.1: N_0 = 19, dx/dt = 1). */
@@ -496,6 +522,7 @@ void orc_get_populations(void *h, double *f)
  * j = sum e f at every fluid node. */
 static void compute_macros(orc_t *o)
 {
+    ORC_PAR_CELLS
     for (long c = 0; c < o->N; c++) {
         o->P[c] = o->jx[c] = o->jy[c] = o->jz[c] = 0.0;
         if (o->node[c] != N_FLUID)
@@ -564,6 +591,7 @@ static void ib_force(orc_t *o)
         for (int a = 0; a < 3; a++)
             o->Vf[3 * s + a] = Vf[a];
     }
+    ORC_PAR_CELLS
     for (long c = 0; c < o->N; c++) {
         int fl = o->node[c] == N_FLUID;
         o->bx[c] = fl ? o->g[0] : 0.0;
@@ -600,6 +628,7 @@ static void ib_force(orc_t *o)
 /* Eq. v with dt = 1: v = j/rho0 + b/(2 rho0). */
 static void forced_velocity(orc_t *o)
 {
+    ORC_PAR_CELLS
     for (long c = 0; c < o->N; c++) {
         o->vx[c] = o->jx[c] / RHO0 + o->bx[c] / (2.0 * RHO0);
         o->vy[c] = o->jy[c] / RHO0 + o->by[c] / (2.0 * RHO0);
@@ -718,6 +747,7 @@ static void nee_boundary(orc_t *o)
 /* Sub-step 3: BGK collision with forcing (Eq. fi) at every fluid node. */
 static void collide(orc_t *o)
 {
+    ORC_PAR_CELLS
     for (long c = 0; c < o->N; c++) {
         if (o->node[c] != N_FLUID)
             continue;
@@ -740,6 +770,9 @@ static void collide(orc_t *o)
 static void stream(orc_t *o)
 {
     static const int OPP[NQ] = {0, 2, 1, 4, 3, 6, 5, 8, 7, 10, 9, 12, 11, 14, 13, 16, 15, 18, 17};
+    /* every f_i(t) slot is written by exactly one (cell, direction): a push
+     * into a fluid target, or the bounce-back into the own cell */
+    ORC_PAR_CELLS
     for (long c = 0; c < o->N; c++) {
         if (o->node[c] != N_FLUID)
             continue;
