@@ -58,6 +58,8 @@ def parse_args():
                     help="aorta: the full-size elastic-wall case (default); batch: 256 uneven rigid tubes; "
                          "tube: the small 24x24x64 tube the oracle runs in full (latency, not bandwidth)")
     ap.add_argument("--autotune", action="store_true", help="pick block size and occupancy variant first")
+    ap.add_argument("--ib-slabs", type=int, default=0,
+                    help="slabs of the pipelined wall-node step (0: the library's default, 1: one launch per kernel)")
     return ap.parse_args()
 
 
@@ -259,13 +261,14 @@ def main():
     inst = insts[0]
     stream = torch.cuda.Stream(device=local)
     wave_cap = 16384 if args.workload == "batch" else 0
-    lat = Lattice(insts, precision=args.precision, device=local, stream=stream.cuda_stream, wave_capacity=wave_cap)
+    lat = Lattice(insts, precision=args.precision, device=local, stream=stream.cuda_stream, wave_capacity=wave_cap,
+                  ib_slabs=args.ib_slabs)
     info = lat.info()
     tuned = None
     if args.autotune:
         tuned = dict(zip(("block", "min_blocks_per_sm", "cells_per_thread"), lat.autotune(iters=10)))
     cells = info.fluid_cells
-    kernels_per_step = 3 + (2 if info.ib_nodes else 0)
+    kernels_per_step = info.launches_per_step
 
     def barrier():
         torch.cuda.synchronize()
@@ -339,6 +342,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
                 "config": {"workload": desc, "fluid_cells": cells, "stored_cells": info.stored_cells,
                            "ib_nodes": info.ib_nodes, "precision": args.precision, "autotuned": tuned,
+                           "ib_slabs": info.slabs, "launches_per_step": info.launches_per_step,
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "l2": ("inputs L2-resident: a latency figure, not a bandwidth one" if args.workload == "tube"
                                   else "inputs larger than L2 (no flush)")},

@@ -127,6 +127,14 @@ typedef struct {
     int wave_capacity; /* waveform ring-buffer length in steps; 0 = 8192 */
     int block_size;    /* threads per block of the stream-collide kernel, multiple of 32 in [32, 256]; 0 = 128 */
     int ib_threads_per_node; /* threads of the immersed-boundary node kernel per wall node: 1, 2 or 4; 0 = 2 */
+    /* Pipelining of a step with wall nodes over slabs of lattice planes: the
+     * band velocities, the wall-node kernel and stream-collide of neighbouring
+     * slabs overlap on three streams (same arithmetic and results as one
+     * launch per kernel, up to the order of the spreading atomics).
+     * 0 = about 8 slabs, 1 = off, 3..64 = about that many slabs.  Lattices
+     * without wall nodes, with filaments, or too short for 3 slabs of 4 planes
+     * or more take one launch per kernel. */
+    int ib_slabs;
 } lbm_config;
 
 typedef struct lbm_handle lbm_handle;
@@ -142,12 +150,15 @@ typedef struct {
     int64_t device_bytes; /* device memory held by the handle */
     int precision;
     int bytes_per_population;
+    int slabs;             /* slabs of the pipelined step with wall nodes (0: one launch per kernel) */
+    int launches_per_step; /* kernel launches of one step in the step graphs */
 } lbm_info_t;
 
 /* Sizes of the layout lbm_create would build (see lbm_check_config). */
 typedef struct {
     int64_t fluid_cells, stored_cells, box_cells, band_cells, links;
     int64_t ib_nodes, filaments;
+    int64_t slabs; /* slabs of the pipelined step with wall nodes (0: one launch per kernel) */
 } lbm_layout_stats;
 
 /* Host only (no CUDA call, no GPU needed): validates cfg as lbm_create does

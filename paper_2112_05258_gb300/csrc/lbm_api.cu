@@ -78,6 +78,12 @@ struct lbm_handle {
     BcKParams bp{};
     IbKParams ibp{};
     int64_t steps = 0;
+    // slab pipeline of a step with wall nodes (L.slab_*; n_slab = 0: serial step)
+    int n_slab = 0;
+    int32_t *node_order = nullptr;
+    cudaStream_t s_node = nullptr, s_sc = nullptr;  // wall-node kernels, stream-collide
+    std::vector<cudaEvent_t> ev_bm, ev_node, ev_sc;
+    cudaEvent_t ev_fork = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t graph1[2] = {nullptr, nullptr};  // single steps (by parity), for step counts below graph_steps
     // kernel timing
@@ -202,7 +208,49 @@ lbm_status check_config(const lbm_config *cfg, std::string &why) {
     return LBM_OK;
 }
 
+// One step with the wall-node exchange pipelined over slabs (captured into
+// the step graphs only).  Slabs are taken from the highest cells down, so the
+// band velocities start on the lines the previous step finished on.  With
+// the slab rules of build_slabs:
+//   band velocities of slab s        stream A, in slab order
+//   node kernel of slab s            stream N, after the band velocities of
+//                                    slabs s+1, s, s-1 (the last issued: s-1)
+//   stream-collide of slab s         stream C, after the node kernels of
+//                                    slabs s+1, s, s-1
+//   0D boundary kernels              stream A, after all of them
+// The band velocities of slab s clear b there before any node kernel that
+// spreads into it (slabs s-1 .. s+1) runs.
+lbm_status launch_step_slabs(lbm_handle *h) {
+    void *fin = h->f[h->parity], *fout = h->f[1 - h->parity];
+    const int K = h->n_slab;
+    const Layout &L = h->L;
+    CK(h, cudaEventRecord(h->ev_fork, h->stream));
+    CK(h, cudaStreamWaitEvent(h->s_node, h->ev_fork, 0));
+    CK(h, cudaStreamWaitEvent(h->s_sc, h->ev_fork, 0));
+    for (int s = K - 1; s >= 0; s--) {
+        CK(h, launch_band_moments(h->prec, fin, h->kp, h->ibp, L.slab_band[s], L.slab_band[s + 1], h->stream));
+        CK(h, cudaEventRecord(h->ev_bm[s], h->stream));
+    }
+    for (int s = K - 1; s >= 0; s--) {
+        CK(h, cudaStreamWaitEvent(h->s_node, h->ev_bm[std::max(s - 1, 0)], 0));
+        CK(h, launch_ib_nodes(h->prec, h->kp, h->ibp, L.slab_node[s], L.slab_node[s + 1], h->s_node));
+        CK(h, cudaEventRecord(h->ev_node[s], h->s_node));
+    }
+    for (int s = K - 1; s >= 0; s--) {
+        CK(h, cudaStreamWaitEvent(h->s_sc, h->ev_node[std::max(s - 1, 0)], 0));
+        CK(h, launch_stream_collide(h->prec, fin, fout, h->kp, h->block, h->variant, h->s_sc, 1, L.slab_cell[s],
+                                    L.slab_cell[s + 1]));
+        CK(h, cudaEventRecord(h->ev_sc[s], h->s_sc));
+    }
+    CK(h, cudaStreamWaitEvent(h->stream, h->ev_node[0], 0));
+    CK(h, cudaStreamWaitEvent(h->stream, h->ev_sc[0], 0));
+    CK(h, launch_boundary(h->prec, fout, h->kp, h->bp, h->stream));
+    h->parity ^= 1;
+    return LBM_OK;
+}
+
 lbm_status launch_step(lbm_handle *h, bool timed) {
+    if (h->n_slab && !timed) return launch_step_slabs(h);
     void *fin = h->f[h->parity], *fout = h->f[1 - h->parity];
     if (h->ibp.n_nodes) CK(h, launch_ib(h->prec, fin, h->kp, h->ibp, h->stream));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -249,7 +297,7 @@ lbm_status ensure_graph(lbm_handle *h) {
         return st;
     }
     CK(h, e);
-    e = cudaGraphInstantiate(&h->graph[par], g, 0);
+    e = cudaGraphInstantiateWithFlags(&h->graph[par], g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     CK(h, e);
     return LBM_OK;
@@ -269,7 +317,7 @@ lbm_status ensure_graph1(lbm_handle *h) {
         return st;
     }
     CK(h, e);
-    e = cudaGraphInstantiate(&h->graph1[par], g, 0);
+    e = cudaGraphInstantiateWithFlags(&h->graph1[par], g, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(g);
     CK(h, e);
     return LBM_OK;
@@ -328,6 +376,11 @@ lbm_status lbm_check_config(const lbm_config *cfg, lbm_layout_stats *stats, char
         stats->links = (int64_t)L.lk_xb.size();
         stats->ib_nodes = (int64_t)L.ib_dA.size();
         stats->filaments = (int64_t)L.fil_start.size();
+        stats->slabs = 0;
+        if (cfg->ib_slabs != 1) {
+            build_slabs(L, cfg->ib_slabs > 0 ? cfg->ib_slabs : 8);
+            if (!L.slab_cell.empty()) stats->slabs = (int64_t)L.slab_cell.size() - 1;
+        }
     }
     return st;
 }
@@ -532,6 +585,26 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
     h->ibp.fil_start = h->fil_start;
     h->ibp.fil_count = h->fil_count;
     h->ibp.fil_par = h->fil_par;
+    h->ibp.order = nullptr;
+    if (ns && cfg->ib_slabs != 1) {
+        build_slabs(L, cfg->ib_slabs > 0 ? cfg->ib_slabs : 8);
+        if (!L.slab_cell.empty()) {
+            const int K = (int)L.slab_cell.size() - 1;
+            int lo = 0, hi = 0;
+            bool sok = ck(upload(h, &h->node_order, L.node_order), "node order") &&
+                       ck(cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities") &&
+                       ck(cudaStreamCreateWithPriority(&h->s_node, cudaStreamNonBlocking, hi), "streams") &&
+                       ck(cudaStreamCreateWithPriority(&h->s_sc, cudaStreamNonBlocking, lo), "streams") &&
+                       ck(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "events");
+            for (auto *v : {&h->ev_bm, &h->ev_node, &h->ev_sc}) {
+                v->assign(K, nullptr);
+                for (auto &e : *v) sok = sok && ck(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "events");
+            }
+            if (!sok) return bail(LBM_ERR_CUDA, h->err);
+            h->n_slab = K;
+            h->ibp.order = h->node_order;
+        }
+    }
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(LBM_ERR_CUDA, "set-up failed");
     *out = h;
     return LBM_OK;
@@ -1048,6 +1121,17 @@ lbm_status lbm_get_info(lbm_handle *h, lbm_info_t *info) {
     info->device_bytes = h->bytes;
     info->precision = h->prec;
     info->bytes_per_population = h->sbytes;
+    info->slabs = h->n_slab;
+    int n = 0;
+    const Layout &L = h->L;
+    if (h->n_slab) {
+        for (int s = 0; s < h->n_slab; s++)
+            n += (L.slab_band[s + 1] > L.slab_band[s]) + (L.slab_node[s + 1] > L.slab_node[s]) +
+                 (L.slab_cell[s + 1] > L.slab_cell[s]);
+    } else {
+        n = (L.n_stored > 0) + (L.ib_dA.empty() ? 0 : (L.band.empty() ? 0 : 1) + 1 + (L.fil_start.empty() ? 0 : 1));
+    }
+    info->launches_per_step = n + (L.bc.empty() ? 0 : 2);
     return LBM_OK;
 }
 
@@ -1062,6 +1146,12 @@ void lbm_destroy(lbm_handle *h) {
         if (h->graph1[k]) cudaGraphExecDestroy(h->graph1[k]);
     }
     for (auto e : h->ev) cudaEventDestroy(e);
+    for (auto *v : {&h->ev_bm, &h->ev_node, &h->ev_sc})
+        for (auto e : *v)
+            if (e) cudaEventDestroy(e);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->s_node) cudaStreamDestroy(h->s_node);
+    if (h->s_sc) cudaStreamDestroy(h->s_sc);
     if (h->par_ring) {
         for (auto e : h->par_ev) cudaEventDestroy(e);
         cudaFreeHost(h->par_ring);

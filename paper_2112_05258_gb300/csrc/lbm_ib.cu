@@ -18,14 +18,15 @@
 
 namespace lbm {
 
-// Blocks take the band in descending cell order: stream-collide finished on
-// the highest cells, whose lines are still in L2.
+// Entries [t0, t1) of the band list (ascending cells).  Blocks take them in
+// descending cell order: stream-collide finished on the highest cells, whose
+// lines are still in L2.
 template <class S>
-__global__ void k_band_moments(const S *__restrict__ fin, KParams p, IbKParams ib) {
+__global__ void k_band_moments(const S *__restrict__ fin, KParams p, IbKParams ib, int t0, int t1) {
     using R = typename Storage<S>::R;
     using V = typename Vec4<R>::T;
-    const int t = (int)(gridDim.x - 1 - blockIdx.x) * blockDim.x + threadIdx.x;
-    if (t >= ib.n_band) return;
+    const int t = t0 + (int)(gridDim.x - 1 - blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= t1) return;
     const int c = ib.band[t];
     const uint32_t fl = p.flags[c];
     const size_t N = (size_t)p.n;
@@ -85,14 +86,17 @@ __device__ __forceinline__ void vec_atomic_add(double4a *a, double4a v) {
 // of a ring.  The group's partial velocities are summed with butterfly
 // shuffles, which every lane evaluates in the same order, so all lanes
 // compute the same penalty force; lane 0 writes the node state.
+// The kernel takes the wall nodes ib.order[k0 .. k1) (all nodes in index
+// order when ib.order is null).
 template <class S, int TPN>
-__global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib) {
+__global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib, int k0, int k1) {
     using R = typename Storage<S>::R;
     using V = typename Vec4<R>::T;
     constexpr int PL = 4 / TPN;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
-    const int s = gt / TPN, q = gt % TPN;
-    if (s >= ib.n_nodes) return;  // the lanes of a node leave together
+    const int kk = k0 + gt / TPN, q = gt % TPN;
+    if (kk >= k1) return;  // the lanes of a node leave together
+    const int s = ib.order ? ib.order[kk] : kk;
     if (q == 0) {  // lane 0 reads the node state after the gathers: bring it towards L2 meanwhile
         asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.Vs + 3 * s));
         asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.I + 3 * s));
@@ -309,39 +313,38 @@ cudaError_t prepare_filament_kernel(int max_fil) {
     return cudaFuncSetAttribute(k_filament, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)filament_smem(max_fil));
 }
 
-template <class S> static void launch_nodes(const KParams &p, const IbKParams &ib, cudaStream_t st) {
+template <class S> static void launch_nodes(const KParams &p, const IbKParams &ib, int k0, int k1, cudaStream_t st) {
     const int tpn = ib.threads_per_node;
-    const int grid = (int)(((long long)ib.n_nodes * tpn + 127) / 128);
-    if (tpn == 1) k_ib_nodes<S, 1><<<grid, 128, 0, st>>>(p, ib);
-    else if (tpn == 2) k_ib_nodes<S, 2><<<grid, 128, 0, st>>>(p, ib);
-    else k_ib_nodes<S, 4><<<grid, 128, 0, st>>>(p, ib);
+    const int grid = (int)(((long long)(k1 - k0) * tpn + 127) / 128);
+    if (grid == 0) return;
+    if (tpn == 1) k_ib_nodes<S, 1><<<grid, 128, 0, st>>>(p, ib, k0, k1);
+    else if (tpn == 2) k_ib_nodes<S, 2><<<grid, 128, 0, st>>>(p, ib, k0, k1);
+    else k_ib_nodes<S, 4><<<grid, 128, 0, st>>>(p, ib, k0, k1);
+}
+
+cudaError_t launch_band_moments(int prec, const void *fin, const KParams &p, const IbKParams &ib, int t0, int t1,
+                                cudaStream_t st) {
+    const int block = 256;
+    const int gb = (t1 - t0 + block - 1) / block;
+    if (gb <= 0) return cudaSuccess;
+    DISPATCH(prec, (k_band_moments<S><<<gb, block, 0, st>>>(static_cast<const S *>(fin), p, ib, t0, t1)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ib_nodes(int prec, const KParams &p, const IbKParams &ib, int k0, int k1, cudaStream_t st) {
+    DISPATCH(prec, (launch_nodes<S>(p, ib, k0, k1, st)));
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ib(int prec, const void *fin, const KParams &p, const IbKParams &ib, cudaStream_t st) {
     if (ib.n_nodes == 0) return cudaSuccess;
-    const int block = 256;
-    const int gb = (ib.n_band + block - 1) / block;
-    switch (prec) {
-    case 0:
-        if (gb) k_band_moments<float><<<gb, block, 0, st>>>(static_cast<const float *>(fin), p, ib);
-        launch_nodes<float>(p, ib, st);
-        break;
-    case 1:
-        if (gb) k_band_moments<__half><<<gb, block, 0, st>>>(static_cast<const __half *>(fin), p, ib);
-        launch_nodes<__half>(p, ib, st);
-        break;
-    case 2:
-        if (gb) k_band_moments<__nv_bfloat16><<<gb, block, 0, st>>>(static_cast<const __nv_bfloat16 *>(fin), p, ib);
-        launch_nodes<__nv_bfloat16>(p, ib, st);
-        break;
-    default:
-        if (gb) k_band_moments<double><<<gb, block, 0, st>>>(static_cast<const double *>(fin), p, ib);
-        launch_nodes<double>(p, ib, st);
-        break;
-    }
-    if (ib.n_fil)
+    cudaError_t e = launch_band_moments(prec, fin, p, ib, 0, ib.n_band, st);
+    if (e == cudaSuccess) e = launch_ib_nodes(prec, p, ib, 0, ib.n_nodes, st);
+    if (e == cudaSuccess && ib.n_fil) {
         k_filament<<<ib.n_fil, FIL_THREADS, filament_smem(ib.max_fil), st>>>(p, ib);
-    return cudaGetLastError();
+        e = cudaGetLastError();
+    }
+    return e;
 }
 
 }  // namespace lbm

@@ -37,23 +37,12 @@ __host__ __device__ constexpr double wgt(int i) { return i == 0 ? 1.0 / 3.0 : (i
 // index of the neighbour row (y - ey, z - ez) a population i is pulled from
 __host__ __device__ constexpr int nbk(int i) { return (1 - cy(i)) + 3 * (1 - cz(i)); }
 
-// Offset of population i of stored cell c in a population buffer of N cells.
-// Default: structure of arrays, f[i][c].  With LBM_AOSOA = 1: blocks of 32
-// cells holding all 19 populations of the block (f[c / 32][i][c % 32]), so
-// that a warp's reads and writes stay within a few 2.4 KB blocks.  Buffers
-// hold population_cells(N) cells.  19 N < 2^31 keeps offsets in 32 bits.
-#ifndef LBM_AOSOA
-#define LBM_AOSOA 0
-#endif
-__host__ __device__ inline uint32_t pidx(int i, uint32_t c, uint32_t N) {
-#if LBM_AOSOA
-    (void)N;
-    return ((c >> 5) * (uint32_t)NQ + (uint32_t)i) * 32u + (c & 31u);
-#else
-    return (uint32_t)i * N + c;
-#endif
-}
-inline int64_t population_cells(int64_t N) { return LBM_AOSOA ? (N + 31) / 32 * 32 : N; }
+// Offset of population i of stored cell c in a population buffer of N cells:
+// structure of arrays, f[i][c] (the stream-collide kernel addresses the same
+// layout through one base pointer per direction).  19 N < 2^31 keeps
+// offsets in 32 bits.
+__host__ __device__ inline uint32_t pidx(int i, uint32_t c, uint32_t N) { return (uint32_t)i * N + c; }
+inline int64_t population_cells(int64_t N) { return N; }
 
 // Per-cell flag word: bits 0..18 = the pull source of direction i is a rigid
 // wall (halfway bounce-back: read the opposite population of the own cell).
@@ -69,14 +58,17 @@ enum : uint32_t {
 // instance.  nb[k] = off(r') - x0(r') of the neighbour row r' at
 // (y + sy, z + sz) with k = (1 + sy) + 3 (1 + sz), or 0 when absent, so the
 // compact index of the stored cell (x', y + sy, z + sz) is nb[k] + x'.
-struct RowInfo {
+// 64 bytes, so that a kernel reads a whole row entry with four 16-byte loads.
+struct alignas(16) RowInfo {
     int32_t off;
     int32_t x0;
     int32_t len;
     int32_t inst;
     int32_t y, z;
     int32_t nb[9];
+    int32_t pad;
 };
+static_assert(sizeof(RowInfo) == 64, "row entry is four 16-byte words");
 
 struct InstParam {
     double tau;
@@ -149,6 +141,16 @@ struct Layout {
     std::vector<int32_t> fil_nodes, fil_start, fil_count;
     std::vector<double> fil_par;
     int max_fil = 0;
+    // slabs of the wall-node pipeline (empty: one launch per kernel per step):
+    // slab s holds the stored cells [slab_cell[s], slab_cell[s+1]), the band
+    // entries [slab_band[s], slab_band[s+1]) and the wall nodes
+    // node_order[slab_node[s] .. slab_node[s+1])
+    std::vector<int32_t> slab_cell, slab_band, slab_node, node_order;
 };
+
+// Cuts the compact cell range into about `want` slabs for the pipelined step
+// (see build_slabs in lbm_layout.cu); leaves the slab tables empty when the
+// lattice has no wall nodes, has filaments, or gives fewer than 3 slabs.
+void build_slabs(Layout &L, int want);
 
 }  // namespace lbm

@@ -77,6 +77,7 @@ struct IbKParams {
     const uint8_t *pinned;
     void *vband;                // fluid velocity j + b/2 (previous step's b) at band cells, 4 x compute type per cell
     int threads_per_node;       // 1, 2 or 4 threads of the node kernel per wall node
+    const int32_t *order;       // wall nodes grouped by slab (null: index order)
     const int32_t *lines;       // 36 per node: compact index of x = 0 on the support lines
     const uint64_t *mask;       // 4 per node: fluid cells of the 6^3 box around the reference cell
     const int32_t *ref;         // 3 per node: reference cell floor(X0 - 0.5)
@@ -91,8 +92,9 @@ struct IbKParams {
 constexpr int SC_VARIANTS = 5;
 int stream_collide_min_blocks(int variant);
 int stream_collide_cells_per_thread(int variant);
+// stream-collide of the stored cells [c0, c1) (c1 < 0: all cells)
 cudaError_t launch_stream_collide(int prec, const void *fin, void *fout, const KParams &p, int block,
-                                  int variant, cudaStream_t s, int desc = 0);
+                                  int variant, cudaStream_t s, int desc = 0, int c0 = 0, int c1 = -1);
 cudaError_t launch_boundary(int prec, void *f, const KParams &p, const BcKParams &q, cudaStream_t s);
 cudaError_t launch_gather(int prec, const void *fin, const KParams &p, int c0, int c1, double *f19, double *mac4,
                           cudaStream_t s);
@@ -110,6 +112,10 @@ cudaError_t launch_cycle_change(const BcKParams &q, const int *bc_first, const i
 cudaError_t launch_init(int prec, void *fout, const KParams &p, const double *f19, int c0, int c1,
                         cudaStream_t s);
 cudaError_t launch_ib(int prec, const void *fin, const KParams &p, const IbKParams &ib, cudaStream_t s);
+// the band-velocity pass over band-list entries [t0, t1), the node kernel over ib.order[k0 .. k1)
+cudaError_t launch_band_moments(int prec, const void *fin, const KParams &p, const IbKParams &ib, int t0, int t1,
+                                cudaStream_t s);
+cudaError_t launch_ib_nodes(int prec, const KParams &p, const IbKParams &ib, int k0, int k1, cudaStream_t s);
 cudaError_t prepare_filament_kernel(int max_fil);
 
 }  // namespace lbm

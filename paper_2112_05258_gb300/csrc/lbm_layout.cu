@@ -334,4 +334,91 @@ std::string build_layout(const lbm_config *cfg, Layout &L) {
     return "";
 }
 
+// Slabs of the pipelined step with wall nodes.  The compact cells are cut at
+// the first row of lattice planes z = 0, 4, 8, ... of an instance, about
+// n_stored / want cells apart, so that within an instance two cuts are at
+// least 4 planes apart.  A wall node belongs to the slab of its reference
+// plane; its kernel support (the 6^3 box around the reference cell, planes
+// z_ref - 2 .. z_ref + 3) then lies in its own slab and the two next to it,
+// and a pull reaches one plane, so:
+//   * the band velocities of slab s read populations of slabs s-1 .. s+1;
+//   * the node kernel of slab s gathers and spreads only in slabs s-1 .. s+1;
+//   * stream-collide of slab s needs the spreading of slabs s-1 .. s+1.
+// The second of these is checked here for every node against its support
+// table; if it failed the tables stay empty (serial step).  Filaments couple
+// nodes along the whole vessel, so they keep the serial step.
+void build_slabs(Layout &L, int want) {
+    L.slab_cell.clear();
+    L.slab_band.clear();
+    L.slab_node.clear();
+    L.node_order.clear();
+    const int64_t ns = (int64_t)L.ib_dA.size();
+    if (want < 3 || ns == 0 || !L.fil_start.empty() || L.n_stored == 0) return;
+    const int64_t target = std::max<int64_t>(1, L.n_stored / want);
+    std::vector<int32_t> cut = {0};
+    const size_t nrow = L.rows.size() - 1;  // without the sentinel
+    for (size_t r = 1; r < nrow; r++) {
+        const RowInfo &ri = L.rows[r], &rp = L.rows[r - 1];
+        const bool plane_start = rp.z != ri.z || rp.inst != ri.inst;
+        if (!plane_start || (ri.z % 4) != 0) continue;
+        if ((int64_t)ri.off - cut.back() >= target) cut.push_back(ri.off);
+    }
+    cut.push_back((int32_t)L.n_stored);
+    const int K = (int)cut.size() - 1;
+    if (K < 3) return;
+    auto slab_of_cell = [&](int64_t c) {
+        return (int)(std::upper_bound(cut.begin(), cut.end(), (int32_t)c) - cut.begin()) - 1;
+    };
+    // slab of every plane of every instance: that of its first stored row, or
+    // of the nearest plane above with rows
+    std::vector<std::vector<int>> plane_slab(L.inst.size());
+    for (size_t q = 0; q < L.inst.size(); q++) plane_slab[q].assign((size_t)std::max(1, L.inst[q].nz), -1);
+    for (size_t r = 0; r < nrow; r++) {
+        const RowInfo &ri = L.rows[r];
+        int &ps = plane_slab[ri.inst][ri.z];
+        if (ps < 0) ps = slab_of_cell(ri.off);
+    }
+    for (size_t q = 0; q < L.inst.size(); q++) {
+        auto &v = plane_slab[q];
+        int next = K - 1;
+        for (int z = (int)v.size() - 1; z >= 0; z--) {
+            if (v[z] < 0) v[z] = next;
+            next = v[z];
+        }
+    }
+    std::vector<int> node_slab((size_t)ns);
+    std::vector<int64_t> per(K + 1, 0);
+    size_t node0 = 0;
+    for (size_t q = 0; q < L.inst.size(); q++) {
+        const InstParam &ip = L.inst[q];
+        for (int k = 0; k < ip.n_ib; k++) {
+            const size_t s = node0 + k;
+            const int z = std::min(std::max(L.ib_ref[3 * s + 2], 0), ip.nz - 1);
+            const int sl = plane_slab[q][z];
+            // every stored cell of the support box must lie in slabs sl - 1 .. sl + 1
+            for (int j = 0; j < 36; j++) {
+                const int64_t base = L.ib_lines[36 * s + j];
+                for (int jx = 0; jx < 6; jx++) {
+                    const int bit = jx + 6 * j;
+                    if (!((L.ib_mask[4 * s + (bit >> 6)] >> (bit & 63)) & 1ull)) continue;
+                    const int cs = slab_of_cell(base + L.ib_ref[3 * s] - 2 + jx);
+                    if (cs < sl - 1 || cs > sl + 1) return;  // keep the serial step
+                }
+            }
+            node_slab[s] = sl;
+            per[sl + 1]++;
+        }
+        node0 += (size_t)ip.n_ib;
+    }
+    for (int k = 0; k < K; k++) per[k + 1] += per[k];
+    L.node_order.assign((size_t)ns, 0);
+    std::vector<int64_t> fill(per.begin(), per.end() - 1);
+    for (int64_t s = 0; s < ns; s++) L.node_order[fill[node_slab[s]]++] = (int32_t)s;  // stable within a slab
+    L.slab_cell = cut;
+    for (int k = 0; k <= K; k++) {
+        L.slab_node.push_back((int32_t)per[k]);
+        L.slab_band.push_back((int32_t)(std::lower_bound(L.band.begin(), L.band.end(), cut[k]) - L.band.begin()));
+    }
+}
+
 }  // namespace lbm

@@ -49,7 +49,7 @@ class Config(ctypes.Structure):
                 ("inst", ctypes.POINTER(InstanceDesc)), ("stream", ctypes.c_void_p),
                 ("device", ctypes.c_int), ("graph_steps", ctypes.c_int),
                 ("wave_capacity", ctypes.c_int), ("block_size", ctypes.c_int),
-                ("ib_threads_per_node", ctypes.c_int)]
+                ("ib_threads_per_node", ctypes.c_int), ("ib_slabs", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -57,12 +57,13 @@ class Info(ctypes.Structure):
                 ("box_cells", ctypes.c_int64), ("band_cells", ctypes.c_int64),
                 ("ib_nodes", ctypes.c_int64), ("links", ctypes.c_int64), ("steps", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("precision", ctypes.c_int),
-                ("bytes_per_population", ctypes.c_int)]
+                ("bytes_per_population", ctypes.c_int), ("slabs", ctypes.c_int),
+                ("launches_per_step", ctypes.c_int)]
 
 
 class LayoutStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in (
-        "fluid_cells", "stored_cells", "box_cells", "band_cells", "links", "ib_nodes", "filaments")]
+        "fluid_cells", "stored_cells", "box_cells", "band_cells", "links", "ib_nodes", "filaments", "slabs")]
 
 
 EXPORTS = ["lbm_create", "lbm_set_0d_params", "lbm_init_populations", "lbm_step", "lbm_sync",
@@ -140,7 +141,7 @@ def _p(a: np.ndarray):
 
 
 def _config(instances, precision, device=0, stream=None, graph_steps=0, wave_capacity=0, block_size=0,
-            ib_threads_per_node=0):
+            ib_threads_per_node=0, ib_slabs=0):
     """lbm_config for the instances and the host arrays it points to (to be
     kept alive while the library copies them)."""
     keep = []
@@ -195,17 +196,17 @@ def _config(instances, precision, device=0, stream=None, graph_steps=0, wave_cap
                  inst=ctypes.cast(descs, ctypes.POINTER(InstanceDesc)),
                  stream=ctypes.c_void_p(stream or 0), device=device, graph_steps=graph_steps,
                  wave_capacity=wave_capacity, block_size=block_size,
-                 ib_threads_per_node=ib_threads_per_node)
+                 ib_threads_per_node=ib_threads_per_node, ib_slabs=ib_slabs)
     keep.append(descs)
     return cfg, keep
 
 
-def check_config(instances, precision="f32", ib_threads_per_node: int = 0) -> dict:
+def check_config(instances, precision="f32", ib_threads_per_node: int = 0, ib_slabs: int = 0) -> dict:
     """Host-only validation and layout sizes of a batch (no GPU needed):
     raises LBMError with the reason if lbm_create would reject it."""
     if isinstance(precision, str):
         precision = PRECISIONS[precision.lower()]
-    cfg, keep = _config(instances, precision, ib_threads_per_node=ib_threads_per_node)
+    cfg, keep = _config(instances, precision, ib_threads_per_node=ib_threads_per_node, ib_slabs=ib_slabs)
     st = LayoutStats()
     why = ctypes.create_string_buffer(512)
     rc = load().lbm_check_config(ctypes.byref(cfg), ctypes.byref(st), why, len(why))
@@ -223,12 +224,12 @@ class Lattice:
 
     def __init__(self, instances: Sequence, precision="f32", device: int = 0,
                  stream: Optional[int] = None, graph_steps: int = 0, wave_capacity: int = 0,
-                 block_size: int = 0, ib_threads_per_node: int = 0):
+                 block_size: int = 0, ib_threads_per_node: int = 0, ib_slabs: int = 0):
         L = load()
         if isinstance(precision, str):
             precision = PRECISIONS[precision.lower()]
         cfg, self._keep = _config(instances, precision, device, stream, graph_steps, wave_capacity,
-                                  block_size, ib_threads_per_node)
+                                  block_size, ib_threads_per_node, ib_slabs)
         self.shapes = [(inst.node.shape[2], inst.node.shape[1], inst.node.shape[0]) for inst in instances]
         self.nbc = [len(inst.boundaries) for inst in instances]
         n = len(instances)

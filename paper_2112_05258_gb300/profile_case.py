@@ -31,6 +31,8 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--nd", type=int, default=512, help="axi: nodes per diameter of the straight aorta")
     ap.add_argument("--warmup", type=int, default=0, help="steps run before the timed ones")
+    ap.add_argument("--ib-slabs", type=int, default=1,
+                    help="slabs of the pipelined wall-node step (1: one launch per kernel, the profiling default)")
     args = ap.parse_args()
     from paper_2112_05258_gb300 import Lattice
     from workloads import aorta, configs
@@ -64,7 +66,8 @@ def main():
     else:
         inst = aorta.build(0)
     lat = Lattice(insts or [inst], precision=args.precision, block_size=args.block,
-                  graph_steps=2 * (args.steps + 1))  # graphs longer than the run: single-step graphs only
+                  graph_steps=2 * (args.steps + 1),  # graphs longer than the run: single-step graphs only
+                  ib_slabs=args.ib_slabs)
     info = lat.info()
     t0 = time.perf_counter()
     lat.step(args.steps)
