@@ -58,8 +58,9 @@ def parse_args():
                     help="aorta: the full-size elastic-wall case (default); batch: 256 uneven rigid tubes; "
                          "tube: the small 24x24x64 tube the oracle runs in full (latency, not bandwidth)")
     ap.add_argument("--autotune", action="store_true", help="pick block size and occupancy variant first")
+    ap.add_argument("--ib-tpn", type=int, default=0, help="threads per wall node of the node kernel (0: default 2)")
     ap.add_argument("--ib-slabs", type=int, default=0,
-                    help="slabs of the pipelined wall-node step (0: the library's default, 1: one launch per kernel)")
+                    help="slabs of the pipelined wall-node step (0 or 1: one launch per kernel, the library's default)")
     return ap.parse_args()
 
 
@@ -262,7 +263,7 @@ def main():
     stream = torch.cuda.Stream(device=local)
     wave_cap = 16384 if args.workload == "batch" else 0
     lat = Lattice(insts, precision=args.precision, device=local, stream=stream.cuda_stream, wave_capacity=wave_cap,
-                  ib_slabs=args.ib_slabs)
+                  ib_slabs=args.ib_slabs, ib_threads_per_node=args.ib_tpn)
     info = lat.info()
     tuned = None
     if args.autotune:

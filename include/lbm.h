@@ -131,9 +131,10 @@ typedef struct {
      * band velocities, the wall-node kernel and stream-collide of neighbouring
      * slabs overlap on three streams (same arithmetic and results as one
      * launch per kernel, up to the order of the spreading atomics).
-     * 0 = about 8 slabs, 1 = off, 3..64 = about that many slabs.  Lattices
-     * without wall nodes, with filaments, or too short for 3 slabs of 4 planes
-     * or more take one launch per kernel. */
+     * 0 or 1 = off (one launch per kernel per step: the default, measured
+     * faster on the elastic-wall aorta), 3..64 = about that many slabs.
+     * Lattices without wall nodes, with filaments, or too short for 3 slabs of
+     * 4 planes or more take one launch per kernel. */
     int ib_slabs;
 } lbm_config;
 

@@ -377,8 +377,8 @@ lbm_status lbm_check_config(const lbm_config *cfg, lbm_layout_stats *stats, char
         stats->ib_nodes = (int64_t)L.ib_dA.size();
         stats->filaments = (int64_t)L.fil_start.size();
         stats->slabs = 0;
-        if (cfg->ib_slabs != 1) {
-            build_slabs(L, cfg->ib_slabs > 0 ? cfg->ib_slabs : 8);
+        if (cfg->ib_slabs > 1) {
+            build_slabs(L, cfg->ib_slabs);
             if (!L.slab_cell.empty()) stats->slabs = (int64_t)L.slab_cell.size() - 1;
         }
     }
@@ -586,8 +586,8 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
     h->ibp.fil_count = h->fil_count;
     h->ibp.fil_par = h->fil_par;
     h->ibp.order = nullptr;
-    if (ns && cfg->ib_slabs != 1) {
-        build_slabs(L, cfg->ib_slabs > 0 ? cfg->ib_slabs : 8);
+    if (ns && cfg->ib_slabs > 1) {
+        build_slabs(L, cfg->ib_slabs);
         if (!L.slab_cell.empty()) {
             const int K = (int)L.slab_cell.size() - 1;
             int lo = 0, hi = 0;

@@ -223,6 +223,25 @@ def test_graph_equals_direct_launches_with_ib(Lattice, filaments):
         assert np.abs(g.waves(0)[:, 1:] - d.waves(0)[:, 1:]).max() < tol
 
 
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-14), ("f32", 1e-6)])
+def test_slab_pipeline_equals_serial_step(Lattice, prec, tol):
+    # the wall-node exchange pipelined over 6 slabs of lattice planes on three
+    # streams: the same kernels and arithmetic as the serial step, only the
+    # order of the spreading atomics may differ
+    inst = configs.ib_tube()
+    a = Lattice([inst], precision=prec, ib_slabs=8)
+    assert a.info().slabs == 6 and a.info().launches_per_step == 6 * 3 + 2
+    a.step(203)
+    b = Lattice([inst], precision=prec)
+    assert b.info().slabs == 0
+    b.step(203)
+    assert np.abs(a.populations(0) - b.populations(0)).max() < tol
+    assert np.abs(a.waves(0)[:, 1:] - b.waves(0)[:, 1:]).max() < tol
+    n = inst.ib.n
+    for x, y in zip(a.ib_state(0, n), b.ib_state(0, n)):
+        assert np.abs(x - y).max() < tol
+
+
 def test_unstable_state_is_reported(Lattice):
     from paper_2112_05258_gb300 import LBMError
     inst = Instance(node=geometry.closed_box(10, 10, 10), tau=0.52)

@@ -23,11 +23,11 @@ def test_ib_tube_layout(check, filaments):
     assert st["filaments"] == (len(inst.ib.filaments) if filaments else 0)
     assert st["fluid_cells"] == inst.n_fluid
     assert 0 < st["band_cells"] <= inst.n_fluid
-    # the slab pipeline (cuts at planes 4, 8, ..., 20 of the 24-plane tube;
-    # every wall node's support passes the slab check); filaments keep the
-    # serial step
-    assert st["slabs"] == (0 if filaments else 6)
-    assert check([inst], ib_slabs=1)["slabs"] == 0
+    # the slab pipeline, when asked for (cuts at planes 4, 8, ..., 20 of the
+    # 24-plane tube; every wall node's support passes the slab check);
+    # filaments keep the serial step
+    assert st["slabs"] == 0
+    assert check([inst], ib_slabs=8)["slabs"] == (0 if filaments else 6)
 
 
 def test_aorta_layout(check):
@@ -35,7 +35,8 @@ def test_aorta_layout(check):
     st = check([inst])
     assert st["fluid_cells"] == 4019584 and st["ib_nodes"] == 204566
     assert st["stored_cells"] < st["box_cells"] / 4      # the compact rows skip the solid
-    assert st["slabs"] == 8 and check([inst], ib_slabs=16)["slabs"] == 16
+    assert st["slabs"] == 0
+    assert check([inst], ib_slabs=8)["slabs"] == 8 and check([inst], ib_slabs=16)["slabs"] == 16
 
 
 def test_batch_sizes_add_up(check):
