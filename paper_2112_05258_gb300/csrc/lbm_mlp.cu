@@ -1,7 +1,7 @@
-// Warm-start network on the GPU: BF16 tensor-core matrix products
-// (mma.sync m16n8k16, FP32 accumulation) with fused epilogues, SiLU hidden
-// layers, mean-squared-error loss, backpropagation and Adam, all in the
-// kernels below.  Contract in include/lbm_mlp.h.
+// Warm-start network on the GPU: BF16 tensor-core matrix products (tcgen05
+// MMA with the accumulator in tensor memory, FP32 accumulation) with fused
+// epilogues, SiLU hidden layers, mean-squared-error loss, backpropagation
+// and Adam, all in the kernels below.  Contract in include/lbm_mlp.h.
 //
 // Every product is C[M][N] = A[M][K] * Bt[N][K]^T with both operands stored
 // K-contiguous ("NT"):
@@ -22,9 +22,12 @@
 
 namespace {
 
+#ifndef LBM_MLP_MMA_SYNC
+#define LBM_MLP_MMA_SYNC 0  // 1: the warp-level mma.sync products instead of tcgen05 (for comparison)
+#endif
+
 using bf16 = __nv_bfloat16;
 constexpr int K0 = 16;       // padded input width
-constexpr int TM = 64, TN = 64, TK = 32;
 
 enum { EPI_HIDDEN = 0, EPI_OUT = 1, EPI_DX = 2, EPI_DW = 3 };
 
@@ -41,6 +44,9 @@ __device__ __forceinline__ float silu_grad_f(float z) {
     const float s = 1.f / (1.f + __expf(-z));
     return s * (1.f + z * (1.f - s));
 }
+
+#if LBM_MLP_MMA_SYNC
+constexpr int TM = 64, TN = 64, TK = 32;
 
 __device__ __forceinline__ void mma_bf16(float *d, const uint32_t *a, const uint32_t *b) {
     asm volatile(
@@ -141,6 +147,198 @@ __global__ void __launch_bounds__(128) k_gemm_nt(const bf16 *__restrict__ A, con
                     }
                 }
             }
+}
+#endif  // LBM_MLP_MMA_SYNC
+
+// ---------------------------------------------------------------------------
+// tcgen05 product C[M][N] = A[M][K] * Bt[N][K]^T (BF16 operands, FP32
+// accumulator in tensor memory).  One CTA of 128 threads per 128 x NT tile of
+// C (NT = 32 or 16 columns).  The K range is walked in chunks of 64 through
+// two shared-memory stages: the four warps copy chunk j's A tile (128 rows)
+// and B tile (NT rows) from global memory into stage j % 2 while the tensor
+// core still works on chunk j - 1.  The tiles are laid out in the canonical
+// no-swizzle K-major form of the tensor-core descriptors: 8-row x 16-byte
+// core matrices, element (r, k) of a tile at byte
+// ((r / 8) * 8 + k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2, so that the core
+// matrix next in K is 128 bytes on (the descriptor's leading-dimension
+// offset) and the next 8-row group 1024 bytes on (its stride offset).  One
+// thread issues one MMA (M = 128, N = NT, K = 16) per 16 columns of the chunk
+// and commits them to the stage's mbarrier, which the copy of chunk j + 2
+// waits for.  After the last chunk each warp reads its 32 rows of the
+// accumulator (tensor-memory lanes 32 w .. 32 w + 31) with tcgen05.ld and
+// applies the epilogue.  Rows >= M and columns >= N are computed from zeros
+// and not stored.  Every wait is bounded: on a time-out the kernel sets
+// *err, waits (bounded) for its own MMAs, frees its tensor memory and leaves.
+constexpr int TC_M = 128, TC_K = 64;
+constexpr int TC_THREADS = 128;
+constexpr long long TC_SPIN = 1ll << 22;  // mbarrier polls before a time-out
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// shared-memory matrix descriptor: start address, leading (K) and stride (M/N)
+// byte offsets, the fixed 0b001 at bits 46-48, no swizzle (bits 61-63 = 0)
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo & 0x3FFFFu) >> 4) << 16) |
+           ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | (1ull << 46);
+}
+
+// instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A
+// and B (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at
+// bits 24-28
+template <int NT> __device__ __forceinline__ uint32_t tc_idesc() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+    for (long long it = 0; it < TC_SPIN; it++) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\n"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(phase)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+template <int EPI> __device__ __forceinline__ void epi_store(const Epi &e, int row, int col, int N, float v) {
+    const size_t idx = (size_t)row * N + col;
+    if (EPI == EPI_HIDDEN) {
+        const float z = v + e.bias[col];
+        e.pre[idx] = z;
+        e.out_bf[idx] = __float2bfloat16_rn(silu_f(z));
+    } else if (EPI == EPI_OUT) {
+        e.out_f[idx] = v + e.bias[col];
+    } else if (EPI == EPI_DX) {
+        const float gr = v * silu_grad_f(e.pre_in[idx]);
+        e.out_f[idx] = gr;
+        e.out_bf[idx] = __float2bfloat16_rn(gr);
+    } else {
+        e.out_f[idx] = v;
+    }
+}
+
+template <int EPI, int NT>
+__global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const bf16 *__restrict__ A, const bf16 *__restrict__ Bt,
+                                                        int M, int N, int K, Epi e, int *err) {
+    constexpr int TMEM_COLS = 32;  // NT <= 32 accumulator columns (the minimum allocation)
+    constexpr int A_BYTES = TC_M * TC_K * 2, B_BYTES = NT * TC_K * 2;
+    static_assert(NT == 16 || NT == 32, "tile width");
+    __shared__ __align__(1024) uint8_t sA[2][A_BYTES];
+    __shared__ __align__(1024) uint8_t sB[2][B_BYTES];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int failed;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * NT;
+    const uint32_t bar_a[2] = {smem_u32(&bar[0]), smem_u32(&bar[1])};
+    if (tid == 0) {
+        failed = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a[0]));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a[1]));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = tc_idesc<NT>();
+    const int nchunk = (K + TC_K - 1) / TC_K;
+    bool ok = true;
+    int last = -1;  // the last chunk whose MMAs were committed
+    for (int j = 0; j < nchunk && ok; j++) {
+        const int st = j & 1, k0 = j * TC_K;
+        // the stage was last read by the MMAs of chunk j - 2
+        if (j >= 2 && !mbar_wait(bar_a[st], ((j - 2) >> 1) & 1)) atomicExch(&failed, 1);
+        __syncthreads();
+        if (failed) {
+            ok = false;
+            break;
+        }
+        // A tile: 128 rows x 8 chunks of 16 bytes; B tile: NT rows x 8 chunks
+        for (int q = tid; q < (TC_M + NT) * (TC_K / 8); q += TC_THREADS) {
+            const bool isA = q < TC_M * (TC_K / 8);
+            const int qq = isA ? q : q - TC_M * (TC_K / 8);
+            const int r = qq >> 3, kc = qq & 7;
+            const int grow = (isA ? m0 : n0) + r, gk = k0 + kc * 8;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (grow < (isA ? M : N) && gk < K)
+                v = *reinterpret_cast<const uint4 *>((isA ? A : Bt) + (size_t)grow * K + gk);
+            uint8_t *dst = (isA ? sA[st] : sB[st]) + (((r >> 3) * 8 + kc) * 128 + (r & 7) * 16);
+            *reinterpret_cast<uint4 *>(dst) = v;
+        }
+        // make the generic-proxy shared stores visible to the tensor core
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_base = smem_u32(sA[st]), b_base = smem_u32(sB[st]);
+            const int nk = min(TC_K / 16, (K - k0 + 15) / 16);
+            for (int kk = 0; kk < nk; kk++) {
+                const uint64_t ad = tc_desc(a_base + kk * 256, 128, 1024);
+                const uint64_t bd = tc_desc(b_base + kk * 256, 128, 1024);
+                const uint32_t acc = (k0 > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\n"
+                    "setp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             bar_a[st])
+                         : "memory");
+        }
+        last = j;
+    }
+    // the last commit completes when all MMAs issued before it have completed
+    if (last >= 0 && !mbar_wait(bar_a[last & 1], (last >> 1) & 1)) atomicExch(&failed, 1);
+    __syncthreads();
+    if (failed) ok = false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        // epilogue: warp w holds rows 32 w .. 32 w + 31 (tensor-memory lanes), 16 columns per load
+        const int row = m0 + warp * 32 + (tid & 31);
+#pragma unroll
+        for (int c0 = 0; c0 < NT; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];\n"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < M) {
+#pragma unroll
+                for (int jj = 0; jj < 16; jj++) {
+                    const int col = n0 + c0 + jj;
+                    if (col < N) epi_store<EPI>(e, row, col, N, __uint_as_float(r[jj]));
+                }
+            }
+        }
+    } else {
+        if (tid == 0) atomicExch(err, 1);
+        // the MMAs still in flight (bounded; their commit was the last one)
+        if (last >= 0) mbar_wait(bar_a[last & 1], (last >> 1) & 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    }
 }
 
 __global__ void k_transpose_bf16(const bf16 *__restrict__ in, bf16 *__restrict__ out, int R, int C) {
@@ -262,6 +460,7 @@ struct lbm_mlp {
     int n_data = 0;
     int32_t *idx = nullptr;
     int64_t adam_steps = 0;
+    int *err = nullptr;                   // device: set by a tensor-core product that timed out
     std::vector<void *> allocs;
 };
 
@@ -288,8 +487,18 @@ template <class T> cudaError_t dal(lbm_mlp *h, T **p, size_t n) {
     } while (0)
 
 template <int EPI> cudaError_t gemm(lbm_mlp *h, const bf16 *A, const bf16 *Bt, int M, int N, int K, const Epi &e) {
+#if LBM_MLP_MMA_SYNC
     dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
     k_gemm_nt<EPI><<<grid, 128, 0, h->stream>>>(A, Bt, M, N, K, e);
+#else
+    if (N % 32 == 0) {
+        dim3 grid(N / 32, (M + TC_M - 1) / TC_M);
+        k_gemm_tc<EPI, 32><<<grid, TC_THREADS, 0, h->stream>>>(A, Bt, M, N, K, e, h->err);
+    } else {
+        dim3 grid((N + 15) / 16, (M + TC_M - 1) / TC_M);
+        k_gemm_tc<EPI, 16><<<grid, TC_THREADS, 0, h->stream>>>(A, Bt, M, N, K, e, h->err);
+    }
+#endif
     return cudaGetLastError();
 }
 
@@ -364,6 +573,17 @@ lbm_status load_input(lbm_mlp *h, const float *x, int B) {
 
 bool bad_batch(const lbm_mlp *h, int B) { return !h || B < 16 || B % 16 || B > h->max_batch; }
 
+// after a synchronisation: a tensor-core product that gave up waiting
+lbm_status check_err(lbm_mlp *h) {
+    int e = 0;
+    MCK(cudaMemcpy(&e, h->err, sizeof e, cudaMemcpyDeviceToHost));
+    if (e) {
+        fprintf(stderr, "lbm_mlp: a tensor-core product timed out waiting for its MMAs\n");
+        return LBM_ERR_CUDA;
+    }
+    return LBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -409,7 +629,8 @@ lbm_status lbm_mlp_create(int n_in, int hidden, int n_hidden, int n_out, int max
               dal(h, &h->m, off) == cudaSuccess && dal(h, &h->v, off) == cudaSuccess &&
               dal(h, &h->dw, maxw) == cudaSuccess && dal(h, &h->y, (size_t)max_batch * n_out) == cudaSuccess &&
               dal(h, &h->t, (size_t)max_batch * n_out) == cudaSuccess &&
-              dal(h, &h->row_loss, max_batch) == cudaSuccess && dal(h, &h->idx, max_batch) == cudaSuccess;
+              dal(h, &h->row_loss, max_batch) == cudaSuccess && dal(h, &h->idx, max_batch) == cudaSuccess &&
+              dal(h, &h->err, 1) == cudaSuccess;
     h->Wt.resize(h->n_layers);
     h->W.resize(h->n_layers);
     h->act.resize(h->n_layers + 1);
@@ -469,7 +690,7 @@ lbm_status lbm_mlp_forward(lbm_mlp *h, const float *x, int B, float *y) {
     MCK(forward(h, B));
     MCK(cudaMemcpyAsync(y, h->y, (size_t)B * h->n_out * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     MCK(cudaStreamSynchronize(h->stream));
-    return LBM_OK;
+    return check_err(h);
 }
 
 lbm_status lbm_mlp_grad(lbm_mlp *h, const float *x, const float *dy, int B, float *g) {
@@ -487,7 +708,7 @@ lbm_status lbm_mlp_grad(lbm_mlp *h, const float *x, const float *dy, int B, floa
     MCK(backward(h, B));
     MCK(cudaMemcpyAsync(g, h->grad, h->np * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
     MCK(cudaStreamSynchronize(h->stream));
-    return LBM_OK;
+    return check_err(h);
 }
 
 lbm_status lbm_mlp_set_data(lbm_mlp *h, const float *x, const float *t, int n) {
@@ -539,7 +760,7 @@ lbm_status lbm_mlp_train(lbm_mlp *h, const int32_t *order, int n_steps, int B, f
     cudaFree(ord);
     cudaFree(dl);
     MCK(e);
-    return LBM_OK;
+    return check_err(h);
 }
 
 void lbm_mlp_destroy(lbm_mlp *h) {

@@ -33,7 +33,7 @@ def _setup(MLP, seed, n_in=6, hidden=64, n_hidden=3, n_out=16, batch=128):
     shapes = omlp.layer_shapes(n_in, hidden, n_hidden, n_out)
     theta = np.concatenate([np.concatenate([rng.standard_normal(r * c) / np.sqrt(c), 0.1 * rng.standard_normal(r)])
                             for r, c in shapes]).astype(np.float32)
-    net = MLP(n_in, hidden, n_hidden, n_out, max_batch=max(batch, 64))
+    net = MLP(n_in, hidden, n_hidden, n_out, max_batch=(batch + 63) // 64 * 64)
     net.set_params(theta)
     theta_b = theta.astype(np.float64).copy()
     # weights are rounded to BF16 on the GPU, biases stay FP32
@@ -89,3 +89,17 @@ def test_training_reduces_loss(MLP):
     # the trained GPU network generalises like its own training loss
     y = net.forward(X[:256])
     assert np.mean((y - T[:256]) ** 2) < 2 * losses[-20:].mean() + 1e-4
+
+
+@pytest.mark.parametrize("batch", [16, 80, 1040])
+def test_ragged_batches_match_oracle(MLP, batch):
+    # tiles of 128 rows with a ragged last tile (16, 80), several tiles and a
+    # weight-gradient product over 1040 rows (a ragged last K chunk)
+    net, shapes, theta, theta_b, x, rng = _setup(MLP, 3, hidden=256, n_out=64, batch=batch)
+    y = net.forward(x)
+    yo, _ = omlp.forward(theta_b, shapes, bf16_round(x))
+    assert np.abs(y - yo).max() < 2e-2 * np.abs(yo).max()
+    dy = rng.standard_normal((batch, 64)).astype(np.float32) / batch
+    g = net.grad(x, dy).astype(np.float64)
+    go = omlp.grad_from_output(theta_b, shapes, bf16_round(x), bf16_round(dy))
+    assert g @ go / (np.linalg.norm(g) * np.linalg.norm(go)) > 0.999
