@@ -16,7 +16,7 @@ import numpy as np
 
 
 def run_to_periodic(lat, periods, tol: float = 0.01, max_cycles: int = 20, chunk: int = 0,
-                    on_chunk=None):
+                    on_chunk=None, history=None):
     """Advances ``lat`` (a :class:`Lattice`) until all instances are periodic
     or ``max_cycles`` beats of the longest period have run.
 
@@ -24,6 +24,8 @@ def run_to_periodic(lat, periods, tol: float = 0.01, max_cycles: int = 20, chunk
     instance q had simulated when first found periodic (-1 if never), and
     ``steps`` the total steps taken.  ``chunk`` (default: gcd of the periods)
     is the stepping granularity; ``on_chunk(step)`` is called after each chunk.
+    ``history`` (a dict, optional) receives for every instance the list of
+    its cycle-to-cycle changes at each beat end until it is periodic.
     """
     periods = np.asarray(periods, dtype=np.int64)
     if chunk <= 0:
@@ -43,4 +45,7 @@ def run_to_periodic(lat, periods, tol: float = 0.01, max_cycles: int = 20, chunk
             delta = lat.cycle_change(periods)
             ok = at_end & (delta >= 0) & (delta <= tol)
             cycles[ok] = (step - start) // periods[ok]
+            if history is not None:
+                for q in np.flatnonzero(at_end):
+                    history.setdefault(int(q), []).append(float(delta[q]))
     return cycles, step - start

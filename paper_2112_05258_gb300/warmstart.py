@@ -51,9 +51,13 @@ def legendre_basis(s: np.ndarray, n: int = N_MODES) -> np.ndarray:
 
 
 def features(params: np.ndarray) -> np.ndarray:
-    """log R_p, log C, log R_d, E_max, E_min, log T."""
+    """log R_p, log C, log R_d, E_max, E_min, log T; with 8 columns (the six
+    0D parameters, then the tube radius and length) also log R and log L."""
     p = np.asarray(params, dtype=np.float64)
-    return np.stack([np.log(p[:, 0]), np.log(p[:, 1]), np.log(p[:, 2]), p[:, 3], p[:, 4], np.log(p[:, 5])], axis=1)
+    cols = [np.log(p[:, 0]), np.log(p[:, 1]), np.log(p[:, 2]), p[:, 3], p[:, 4], np.log(p[:, 5])]
+    if p.shape[1] >= 8:
+        cols += [np.log(p[:, 6]), np.log(p[:, 7])]
+    return np.stack(cols, axis=1)
 
 
 class Layers:
@@ -116,14 +120,43 @@ def apply(lat, q: int, inst, label: np.ndarray, layers: Layers):
 
 
 def generate(n: int, seed: int, radius=6.0, length=128, period_range=(2000, 6000), kappa=None,
-             precision="f32", max_cycles=20, log=print):
-    """Runs a sweep to periodic state and reads one label per instance."""
+             precision="f32", max_cycles=20, log=print, geometry_sweep=False, batch_size=256,
+             keep_instances=True, radius_range=(6.0, 20.0), length_range=(128, 512)):
+    """Runs a sweep to periodic state and reads one label per instance.
+
+    ``geometry_sweep``: radius and length are drawn per instance over
+    ``radius_range`` and ``length_range`` (by default the batching workload's
+    R in [6, 20], L in [128, 512]) and appended
+    to the returned parameters as columns 6 and 7; the sweep runs in batches
+    of ``batch_size`` instances (batch b drawn with seed 1000 seed + b).
+    Returns (instances or None, params, labels, cycles)."""
+    if not geometry_sweep:
+        return _generate_batch(n, seed, radius, length, period_range, kappa, precision, max_cycles, log, None)
+    insts, params, labels, cycles = [], [], [], []
+    for b, k0 in enumerate(range(0, n, batch_size)):
+        i, p, y, c = _generate_batch(min(batch_size, n - k0), 1000 * seed + b, radius, length, period_range, kappa,
+                                     precision, max_cycles, log, (radius_range, length_range))
+        if keep_instances:
+            insts += i
+        params.append(p)
+        labels.append(y)
+        cycles.append(c)
+    return (insts if keep_instances else None), np.concatenate(params), np.concatenate(labels), \
+        np.concatenate(cycles)
+
+
+def _generate_batch(n, seed, radius, length, period_range, kappa, precision, max_cycles, log, ranges):
     from workloads import batch, configs
     from . import Lattice
     from .periodic import run_to_periodic
     kappa = configs.LV_KAPPA if kappa is None else kappa
-    insts, params = batch.lv_sweep(n, seed, radius=radius, length=length, period_range=period_range,
-                                   kappa=kappa)
+    if ranges is not None:
+        insts, params, geom = batch.lv_geometry_sweep(n, seed, period_range=period_range, kappa=kappa,
+                                                      radius_range=ranges[0], length_range=ranges[1])
+        params = np.concatenate([params, geom], axis=1)
+    else:
+        insts, params = batch.lv_sweep(n, seed, radius=radius, length=length, period_range=period_range,
+                                       kappa=kappa)
     periods = params[:, 5].astype(np.int64)
     chunk = 100 if period_range[0] >= 1000 else 20
     cap = int(2 * periods.max() + 2 * chunk)
@@ -132,13 +165,13 @@ def generate(n: int, seed: int, radius=6.0, length=128, period_range=(2000, 6000
     cycles, steps = run_to_periodic(lat, periods, tol=0.01, max_cycles=max_cycles, chunk=chunk)
     log(f"generate: {n} instances periodic after {steps} steps ({time.perf_counter() - t0:.1f} s); "
         f"cycles median {np.median(cycles):.0f}, unconverged {(cycles < 0).sum()}")
-    layers = Layers(insts[0])
+    layers = [Layers(i) for i in insts]
     labels = np.zeros((n, N_OUT))
     pending = np.ones(n, bool)
     while pending.any():
         at0 = pending & (steps % periods == 0)
         for q in np.flatnonzero(at0):
-            labels[q] = read_label(lat, q, layers)
+            labels[q] = read_label(lat, q, layers[q])
         pending &= ~at0
         if pending.any():
             lat.step(chunk)
@@ -169,8 +202,9 @@ def train(params, labels, hidden=256, n_hidden=3, epochs=300, batch=512, lr=2e-3
     Yn[:, :N_LABEL] = (Y - ym) / ys
     rng = np.random.default_rng(seed)
     batch = max(64, min(batch, (X.shape[0] // 64) * 64))
-    net = MLP(6, hidden, n_hidden, N_OUT, max_batch=max(batch, 64))
-    net.set_params(_init_params(layer_shapes(6, hidden, n_hidden, N_OUT), rng))
+    n_in = X.shape[1]
+    net = MLP(n_in, hidden, n_hidden, N_OUT, max_batch=max(batch, 64))
+    net.set_params(_init_params(layer_shapes(n_in, hidden, n_hidden, N_OUT), rng))
     net.set_data(Xn, Yn)
     n = X.shape[0]
     steps_per_epoch = max(1, n // batch)
@@ -185,7 +219,7 @@ def train(params, labels, hidden=256, n_hidden=3, epochs=300, batch=512, lr=2e-3
     def predict(p):
         Z = ((features(p) - xm) / xs).astype(np.float32)
         nb = ((Z.shape[0] + 63) // 64) * 64
-        Zp = np.zeros((nb, 6), np.float32)
+        Zp = np.zeros((nb, Z.shape[1]), np.float32)
         Zp[:Z.shape[0]] = Z
         out = []
         for k in range(0, nb, net_batch):
@@ -200,14 +234,43 @@ def train(params, labels, hidden=256, n_hidden=3, epochs=300, batch=512, lr=2e-3
     return predict
 
 
-def evaluate(insts, params, predict, precision_warm="f16", max_cycles=20, log=print):
-    """Cold FP32 start vs warm start (mixed precision, and FP32) on held-out sets."""
+def evaluate(insts, params, predict, precision_warm="f16", max_cycles=20, log=print, batch_size=None):
+    """Cold FP32 start vs warm start (mixed precision, and FP32) on held-out sets.
+
+    ``batch_size``: the held-out instances run in consecutive batches of this
+    many (one lattice each, as the batching workload does); wall times add up
+    over the batches and the instance that decides each batch is reported."""
+    n = len(insts)
+    bs = n if not batch_size else int(batch_size)
+    parts = [_evaluate_batch(insts[k:k + bs], params[k:k + bs], predict, precision_warm, max_cycles, log)
+             for k in range(0, n, bs)]
+    res = {}
+    for name in parts[0]:
+        cyc = np.concatenate([np.array(p[name]["cycles"]) for p in parts])
+        ok = cyc >= 0
+        r = {"cycles": cyc.tolist(), "steps": [p[name]["steps"] for p in parts],
+             "wall_s": float(sum(p[name]["wall_s"] for p in parts)),
+             "median_cycles": float(np.median(cyc[ok])) if ok.any() else None,
+             "mean_cycles": float(np.mean(cyc[ok])) if ok.any() else None,
+             "unconverged": int((~ok).sum()),
+             "slowest": [p[name]["slowest"] for p in parts]}
+        if "waveform_diffs" in parts[0][name]:
+            d = np.concatenate([p[name]["waveform_diffs"] for p in parts])
+            r["waveform_diff_vs_cold_max"] = float(d.max())
+            r["waveform_diff_vs_cold_median"] = float(np.median(d))
+            cc = np.concatenate([np.array(p["cold_f32"]["cycles"]) for p in parts])
+            r["fraction_worse_than_cold"] = float(np.mean(cyc > cc))
+        res[name] = r
+    return res
+
+
+def _evaluate_batch(insts, params, predict, precision_warm, max_cycles, log):
     from . import Lattice
     from .periodic import run_to_periodic
     periods = params[:, 5].astype(np.int64)
     chunk = 100 if periods.min() >= 1000 else 20
     cap = int(2 * periods.max() + 2 * chunk)
-    layers = Layers(insts[0])
+    layers = [Layers(i) for i in insts]
     pred = predict(params)
     res = {}
     finals = {}
@@ -216,12 +279,15 @@ def evaluate(insts, params, predict, precision_warm="f16", max_cycles=20, log=pr
         lat = Lattice(insts, precision=prec, wave_capacity=cap, graph_steps=chunk)
         if warm:
             for q in range(len(insts)):
-                apply(lat, q, insts[q], pred[q], layers)
+                apply(lat, q, insts[q], pred[q], layers[q])
         lat.sync()
         t0 = time.perf_counter()
-        cycles, steps = run_to_periodic(lat, periods, tol=0.01, max_cycles=max_cycles, chunk=chunk)
+        hist = {}
+        cycles, steps = run_to_periodic(lat, periods, tol=0.01, max_cycles=max_cycles, chunk=chunk, history=hist)
         lat.sync()
         wall = time.perf_counter() - t0
+        # the instance that decides the batch's wall time: the last to become periodic
+        last = int(np.argmax(np.where(cycles >= 0, cycles * periods, int(steps) + 1)))
         # the periodic waveforms reached: the last whole beat (phase 0 to phase 0)
         fin = []
         for q in range(len(insts)):
@@ -232,10 +298,11 @@ def evaluate(insts, params, predict, precision_warm="f16", max_cycles=20, log=pr
             fin.append(w[sel, 1:])
         finals[name] = fin
         res[name] = {"cycles": cycles.tolist(), "steps": int(steps), "wall_s": wall,
-                     "median_cycles": float(np.median(cycles[cycles >= 0])) if (cycles >= 0).any() else None,
-                     "unconverged": int((cycles < 0).sum())}
-        log(f"{name}: steps {steps}, wall {wall:.2f} s, median cycles {res[name]['median_cycles']}, "
-            f"unconverged {res[name]['unconverged']}")
+                     "slowest": {"instance": last, "params": [float(v) for v in params[last]],
+                                 "cycles": int(cycles[last]), "cycle_changes": hist.get(last, [])}}
+        ok = cycles >= 0
+        log(f"{name}: steps {steps}, wall {wall:.2f} s, median cycles "
+            f"{float(np.median(cycles[ok])) if ok.any() else None}, unconverged {int((~ok).sum())}")
         lat.close()
     # the cold method judges the periodic state reached from the warm start
     for name in ("warm_f32", "warm_" + precision_warm):
@@ -244,10 +311,7 @@ def evaluate(insts, params, predict, precision_warm="f16", max_cycles=20, log=pr
             a, b = finals[name][q], finals["cold_f32"][q]
             cols = [0, 1, 4, 5]
             errs.append(max(np.abs(a[:, c] - b[:, c]).max() / (np.abs(b[:, c]).max() + 1e-30) for c in cols))
-        res[name]["waveform_diff_vs_cold_max"] = float(np.max(errs))
-        res[name]["waveform_diff_vs_cold_median"] = float(np.median(errs))
-        cw, cc = np.array(res[name]["cycles"]), np.array(res["cold_f32"]["cycles"])
-        res[name]["fraction_worse_than_cold"] = float(np.mean(cw > cc))
+        res[name]["waveform_diffs"] = np.array(errs)
     return res
 
 
@@ -258,17 +322,22 @@ def main():
     ap.add_argument("--epochs", type=int, default=300)
     ap.add_argument("--out", default="warmstart.json")
     ap.add_argument("--small", action="store_true", help="short beats and tubes (quick check)")
+    ap.add_argument("--geometry-sweep", action="store_true",
+                    help="radius and length drawn per instance over the batching workload's ranges")
     a = ap.parse_args()
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     kw = {}
     if a.small:
         from workloads import configs
         kw = dict(radius=4.0, length=32, period_range=(400, 800), kappa=configs.LV_KAPPA * 4000 / 600)
+    if a.geometry_sweep:
+        kw["geometry_sweep"] = True
     t0 = time.perf_counter()
-    _, ptr, ytr, _ = generate(a.n_train, 1, **kw)
+    _, ptr, ytr, ctr = generate(a.n_train, 1, keep_instances=False, **kw)
+    np.savez(os.path.splitext(a.out)[0] + "_train.npz", params=ptr, labels=ytr, cycles=ctr)
     predict = train(ptr, ytr, epochs=a.epochs)
     insts, pte, yte, _ = generate(a.n_test, 2, **kw)
-    res = evaluate(insts, pte, predict)
+    res = evaluate(insts, pte, predict, batch_size=256 if a.geometry_sweep else None)
     pred = predict(pte)[:, :N_LABEL]
     spread = yte[:, :N_LABEL].std(0)
     err = np.abs(pred - yte[:, :N_LABEL]).mean(0) / np.where(spread > 0, np.abs(yte[:, :N_LABEL]).mean(0), 1.0)

@@ -11,8 +11,13 @@ in a physiological arterial tree; with the rigid-tube workload's C = 200
 (R_d C = 0.2 of its 1000-step beat) the chamber would empty between beats
 of an LV inlet.
 
-``lv_sweep``: the warm-start workload -- the same six 0D parameters
-(R_p, C, R_d, E_max, E_min, period) drawn for many copies of one small tube.
+``lv_sweep``: the warm-start workload on one geometry -- the same six 0D
+parameters (R_p, C, R_d, E_max, E_min, period) drawn for many copies of one
+small tube.
+
+``lv_geometry_sweep``: the warm-start workload over the batching workload's
+geometries -- radius uniform in [6, 20] and length uniform in [128, 512]
+drawn per instance together with the six 0D parameters.
 """
 from __future__ import annotations
 
@@ -73,3 +78,16 @@ def lv_sweep(n: int, seed: int, radius: float = 6.0, length: int = 128, period_s
     params = draw_params(rng, n, e_min_range=(0.05, 0.07), period_step=period_step,
                          period_range=period_range)
     return [lv_tube_instance(params[q], radius, length, kappa=kappa) for q in range(n)], params
+
+
+def lv_geometry_sweep(n: int, seed: int, period_step: int = 100, period_range=(2000, 6000),
+                      radius_range=(6.0, 20.0), length_range=(128, 512), kappa: float = configs.LV_KAPPA):
+    """Returns (instances, params, geometry) for the warm-start study over the
+    batching workload's geometries: ``geometry[q] = (R, L)``; six 0D
+    parameters drawn per instance as in :func:`lv_sweep`."""
+    rng = np.random.default_rng(seed)
+    params = draw_params(rng, n, e_min_range=(0.05, 0.07), period_step=period_step, period_range=period_range)
+    R = rng.uniform(radius_range[0], radius_range[1], n)
+    L = rng.integers(length_range[0], length_range[1] + 1, n)
+    geom = np.stack([R, L.astype(np.float64)], axis=1)
+    return [lv_tube_instance(params[q], R[q], int(L[q]), kappa=kappa) for q in range(n)], params, geom
