@@ -334,7 +334,7 @@ def main():
            "steps": e2e_steps}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "aorta":
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ("aorta", "tube"):
         cpu = cpu_baseline(inst, args.cpu_seconds)
 
     if rank == 0:
@@ -343,7 +343,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
                 "config": {"workload": desc, "fluid_cells": cells, "stored_cells": info.stored_cells,
                            "ib_nodes": info.ib_nodes, "precision": args.precision, "autotuned": tuned,
-                           "ib_slabs": info.slabs, "launches_per_step": info.launches_per_step,
+                           "ib_slabs": info.slabs,
+                           "launches_per_step": info.launches_per_step,
                            "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                            "l2": ("inputs L2-resident: a latency figure, not a bandwidth one" if args.workload == "tube"
                                   else "inputs larger than L2 (no flush)")},

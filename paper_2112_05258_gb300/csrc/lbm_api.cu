@@ -239,7 +239,7 @@ lbm_status launch_step_slabs(lbm_handle *h) {
     for (int s = K - 1; s >= 0; s--) {
         CK(h, cudaStreamWaitEvent(h->s_sc, h->ev_node[std::max(s - 1, 0)], 0));
         CK(h, launch_stream_collide(h->prec, fin, fout, h->kp, h->block, h->variant, h->s_sc, 1, L.slab_cell[s],
-                                    L.slab_cell[s + 1]));
+                                    L.slab_cell[s + 1], s == 0 ? 1 : 0));
         CK(h, cudaEventRecord(h->ev_sc[s], h->s_sc));
     }
     CK(h, cudaStreamWaitEvent(h->stream, h->ev_node[0], 0));

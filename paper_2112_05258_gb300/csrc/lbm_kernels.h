@@ -92,9 +92,10 @@ struct IbKParams {
 constexpr int SC_VARIANTS = 5;
 int stream_collide_min_blocks(int variant);
 int stream_collide_cells_per_thread(int variant);
-// stream-collide of the stored cells [c0, c1) (c1 < 0: all cells)
+// stream-collide of the stored cells [c0, c1) (c1 < 0: all cells); bump: the
+// launch advances the step counter (one launch per step does)
 cudaError_t launch_stream_collide(int prec, const void *fin, void *fout, const KParams &p, int block,
-                                  int variant, cudaStream_t s, int desc = 0, int c0 = 0, int c1 = -1);
+                                  int variant, cudaStream_t s, int desc = 0, int c0 = 0, int c1 = -1, int bump = 1);
 cudaError_t launch_boundary(int prec, void *f, const KParams &p, const BcKParams &q, cudaStream_t s);
 cudaError_t launch_gather(int prec, const void *fin, const KParams &p, int c0, int c1, double *f19, double *mac4,
                           cudaStream_t s);

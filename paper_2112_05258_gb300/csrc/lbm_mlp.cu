@@ -154,9 +154,9 @@ __global__ void __launch_bounds__(128) k_gemm_nt(const bf16 *__restrict__ A, con
 // tcgen05 product C[M][N] = A[M][K] * Bt[N][K]^T (BF16 operands, FP32
 // accumulator in tensor memory).  One CTA of 128 threads per 128 x NT tile of
 // C (NT = 32 or 16 columns).  The K range is walked in chunks of 64 through
-// two shared-memory stages: the four warps copy chunk j's A tile (128 rows)
-// and B tile (NT rows) from global memory into stage j % 2 while the tensor
-// core still works on chunk j - 1.  The tiles are laid out in the canonical
+// two shared-memory stages: the four warps start the asynchronous copies
+// (cp.async, 16 bytes each) of chunk j + 1's A tile (128 rows) and B tile
+// (NT rows) into stage (j + 1) % 2 before the tensor core works on chunk j.  The tiles are laid out in the canonical
 // no-swizzle K-major form of the tensor-core descriptors: 8-row x 16-byte
 // core matrices, element (r, k) of a tile at byte
 // ((r / 8) * 8 + k / 8) * 128 + (r % 8) * 16 + (k % 8) * 2, so that the core
@@ -166,7 +166,8 @@ __global__ void __launch_bounds__(128) k_gemm_nt(const bf16 *__restrict__ A, con
 // and commits them to the stage's mbarrier, which the copy of chunk j + 2
 // waits for.  After the last chunk each warp reads its 32 rows of the
 // accumulator (tensor-memory lanes 32 w .. 32 w + 31) with tcgen05.ld and
-// applies the epilogue.  Rows >= M and columns >= N are computed from zeros
+// applies the epilogue, 16 consecutive columns of a row per thread with
+// 16-byte loads and stores.  Rows >= M and columns >= N are computed from zeros
 // and not stored.  Every wait is bounded: on a time-out the kernel sets
 // *err, waits (bounded) for its own MMAs, frees its tensor memory and leaves.
 constexpr int TC_M = 128, TC_K = 64;
@@ -206,21 +207,57 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
     return false;
 }
 
-template <int EPI> __device__ __forceinline__ void epi_store(const Epi &e, int row, int col, int N, float v) {
+// Epilogue of 16 consecutive columns col .. col + 15 of one row (col and N
+// multiples of 16): 16-byte vector loads and stores.
+template <int EPI> __device__ __forceinline__ void epi_store16(const Epi &e, int row, int col, int N, const uint32_t *r) {
     const size_t idx = (size_t)row * N + col;
-    if (EPI == EPI_HIDDEN) {
-        const float z = v + e.bias[col];
-        e.pre[idx] = z;
-        e.out_bf[idx] = __float2bfloat16_rn(silu_f(z));
-    } else if (EPI == EPI_OUT) {
-        e.out_f[idx] = v + e.bias[col];
-    } else if (EPI == EPI_DX) {
-        const float gr = v * silu_grad_f(e.pre_in[idx]);
-        e.out_f[idx] = gr;
-        e.out_bf[idx] = __float2bfloat16_rn(gr);
-    } else {
-        e.out_f[idx] = v;
+    float v[16];
+#pragma unroll
+    for (int j = 0; j < 16; j++) v[j] = __uint_as_float(r[j]);
+    if (EPI == EPI_HIDDEN || EPI == EPI_OUT) {
+        const float4 *b4 = reinterpret_cast<const float4 *>(e.bias + col);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const float4 b = b4[q];
+            v[4 * q] += b.x;
+            v[4 * q + 1] += b.y;
+            v[4 * q + 2] += b.z;
+            v[4 * q + 3] += b.w;
+        }
     }
+    if (EPI == EPI_DX) {
+        const float4 *p4 = reinterpret_cast<const float4 *>(e.pre_in + idx);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const float4 z = p4[q];
+            v[4 * q] *= silu_grad_f(z.x);
+            v[4 * q + 1] *= silu_grad_f(z.y);
+            v[4 * q + 2] *= silu_grad_f(z.z);
+            v[4 * q + 3] *= silu_grad_f(z.w);
+        }
+    }
+    float *of = EPI == EPI_HIDDEN ? e.pre : e.out_f;
+    float4 *o4 = reinterpret_cast<float4 *>(of + idx);
+#pragma unroll
+    for (int q = 0; q < 4; q++) o4[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    if (EPI == EPI_HIDDEN || EPI == EPI_DX) {
+        uint32_t w[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const float a = EPI == EPI_HIDDEN ? silu_f(v[2 * q]) : v[2 * q];
+            const float b = EPI == EPI_HIDDEN ? silu_f(v[2 * q + 1]) : v[2 * q + 1];
+            const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+            w[q] = *reinterpret_cast<const uint32_t *>(&h);
+        }
+        uint4 *b4 = reinterpret_cast<uint4 *>(e.out_bf + idx);
+        b4[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        b4[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    }
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
 }
 
 template <int EPI, int NT>
@@ -254,32 +291,41 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const bf16 *__restrict__
     const uint32_t tmem = tmem_base;
     const uint32_t idesc = tc_idesc<NT>();
     const int nchunk = (K + TC_K - 1) / TC_K;
-    bool ok = true;
-    int last = -1;  // the last chunk whose MMAs were committed
-    for (int j = 0; j < nchunk && ok; j++) {
+    // asynchronous copy of chunk j into stage j % 2 (rows or columns past the
+    // matrix are zero-filled): A tile 128 rows x 8 pieces of 16 bytes, B tile NT rows
+    auto copy_chunk = [&](int j) {
         const int st = j & 1, k0 = j * TC_K;
-        // the stage was last read by the MMAs of chunk j - 2
-        if (j >= 2 && !mbar_wait(bar_a[st], ((j - 2) >> 1) & 1)) atomicExch(&failed, 1);
-        __syncthreads();
-        if (failed) {
-            ok = false;
-            break;
-        }
-        // A tile: 128 rows x 8 chunks of 16 bytes; B tile: NT rows x 8 chunks
+        const uint32_t a_s = smem_u32(sA[st]), b_s = smem_u32(sB[st]);
         for (int q = tid; q < (TC_M + NT) * (TC_K / 8); q += TC_THREADS) {
             const bool isA = q < TC_M * (TC_K / 8);
             const int qq = isA ? q : q - TC_M * (TC_K / 8);
             const int r = qq >> 3, kc = qq & 7;
             const int grow = (isA ? m0 : n0) + r, gk = k0 + kc * 8;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (grow < (isA ? M : N) && gk < K)
-                v = *reinterpret_cast<const uint4 *>((isA ? A : Bt) + (size_t)grow * K + gk);
-            uint8_t *dst = (isA ? sA[st] : sB[st]) + (((r >> 3) * 8 + kc) * 128 + (r & 7) * 16);
-            *reinterpret_cast<uint4 *>(dst) = v;
+            const bool valid = grow < (isA ? M : N) && gk < K;
+            const bf16 *src = valid ? (isA ? A : Bt) + (size_t)grow * K + gk : A;
+            cp_async16((isA ? a_s : b_s) + (uint32_t)(((r >> 3) * 8 + kc) * 128 + (r & 7) * 16), src, valid);
         }
-        // make the generic-proxy shared stores visible to the tensor core
+    };
+    bool ok = true;
+    int last = -1;  // the last chunk whose MMAs were committed
+    copy_chunk(0);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    for (int j = 0; j < nchunk && ok; j++) {
+        const int st = j & 1, k0 = j * TC_K;
+        if (j + 1 < nchunk) {
+            // stage (j + 1) % 2 was last read by the MMAs of chunk j - 1
+            if (j >= 1 && !mbar_wait(bar_a[(j + 1) & 1], ((j - 1) >> 1) & 1)) atomicExch(&failed, 1);
+            if (!failed) copy_chunk(j + 1);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 1;" ::: "memory");  // chunk j has landed
+        // make the copies visible to the tensor core
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
+        if (failed) {
+            ok = false;
+            break;
+        }
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a_base = smem_u32(sA[st]), b_base = smem_u32(sB[st]);
@@ -300,6 +346,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const bf16 *__restrict__
         }
         last = j;
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy outlives the kernel
     // the last commit completes when all MMAs issued before it have completed
     if (last >= 0 && !mbar_wait(bar_a[last & 1], (last >> 1) & 1)) atomicExch(&failed, 1);
     __syncthreads();
@@ -320,13 +367,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_gemm_tc(const bf16 *__restrict__
                   "=r"(r[15])
                 : "r"(ta));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < M) {
-#pragma unroll
-                for (int jj = 0; jj < 16; jj++) {
-                    const int col = n0 + c0 + jj;
-                    if (col < N) epi_store<EPI>(e, row, col, N, __uint_as_float(r[jj]));
-                }
-            }
+            if (row < M && n0 + c0 < N) epi_store16<EPI>(e, row, n0 + c0, N, r);  // N is a multiple of 16
         }
     } else {
         if (tid == 0) atomicExch(err, 1);

@@ -131,17 +131,17 @@ __device__ __forceinline__ void collide_store(const PopDirs<S> &d, const KParams
     }
 }
 
-// The launch covers the stored cells [c0, c1); the one whose range starts at
-// cell 0 advances the step counter.
+// The launch covers the stored cells [c0, c1); the launch with bump = 1
+// advances the step counter.
 template <class S, int MINB, int CPT>
 __global__ void __launch_bounds__(256, MINB)
     k_stream_collide(const __grid_constant__ PopDirs<S> d, const __grid_constant__ KParams p, int desc, int c0,
-                     int c1) {
+                     int c1, int bump) {
     using R = typename Storage<S>::R;
     const int bid = desc ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
     const int t = c0 + bid * blockDim.x + threadIdx.x;
     const int stride = gridDim.x * blockDim.x;
-    if (t == 0 && p.step) *p.step += 1;  // the step index t_n seen by the boundary kernels
+    if (bump && t == c0 && p.step) *p.step += 1;  // the step index t_n seen by the boundary kernels
     const int N = (int)p.n;  // 19 N < 2^31 is checked at creation
     R f[CPT][NQ];
     R om[CPT];
@@ -199,7 +199,7 @@ template <class S> static PopDirs<S> pop_dirs(const void *fin, void *fout, long 
 }
 
 cudaError_t launch_stream_collide(int prec, const void *fin, void *fout, const KParams &p, int block,
-                                  int variant, cudaStream_t s, int desc, int c0, int c1) {
+                                  int variant, cudaStream_t s, int desc, int c0, int c1, int bump) {
     if (c1 < 0) c1 = (int)p.n;
     if (c1 <= c0) return cudaSuccess;
     if (block % 32) return cudaErrorInvalidValue;  // whole warps: the forcing branch is a warp vote
@@ -207,19 +207,19 @@ cudaError_t launch_stream_collide(int prec, const void *fin, void *fout, const K
     const int grid = (int)((c1 - c0 + (long long)block * cpt - 1) / ((long long)block * cpt));
     switch (variant) {
     case 1:
-        DISPATCH(prec, (k_stream_collide<S, 8, 1><<<grid, block, 0, s>>>(pop_dirs<S>(fin, fout, p.n), p, desc, c0, c1)));
+        DISPATCH(prec, (k_stream_collide<S, 8, 1><<<grid, block, 0, s>>>(pop_dirs<S>(fin, fout, p.n), p, desc, c0, c1, bump)));
         break;
     case 2:
-        DISPATCH(prec, (k_stream_collide<S, 5, 1><<<grid, block, 0, s>>>(pop_dirs<S>(fin, fout, p.n), p, desc, c0, c1)));
+        DISPATCH(prec, (k_stream_collide<S, 5, 1><<<grid, block, 0, s>>>(pop_dirs<S>(fin, fout, p.n), p, desc, c0, c1, bump)));
         break;
     case 3:
-        DISPATCH(prec, (k_stream_collide<S, 4, 2><<<grid, block, 0, s>>>(pop_dirs<S>(fin, fout, p.n), p, desc, c0, c1)));
+        DISPATCH(prec, (k_stream_collide<S, 4, 2><<<grid, block, 0, s>>>(pop_dirs<S>(fin, fout, p.n), p, desc, c0, c1, bump)));
         break;
     case 4:
-        DISPATCH(prec, (k_stream_collide<S, 3, 2><<<grid, block, 0, s>>>(pop_dirs<S>(fin, fout, p.n), p, desc, c0, c1)));
+        DISPATCH(prec, (k_stream_collide<S, 3, 2><<<grid, block, 0, s>>>(pop_dirs<S>(fin, fout, p.n), p, desc, c0, c1, bump)));
         break;
     default:
-        DISPATCH(prec, (k_stream_collide<S, 6, 1><<<grid, block, 0, s>>>(pop_dirs<S>(fin, fout, p.n), p, desc, c0, c1)));
+        DISPATCH(prec, (k_stream_collide<S, 6, 1><<<grid, block, 0, s>>>(pop_dirs<S>(fin, fout, p.n), p, desc, c0, c1, bump)));
         break;
     }
     return cudaGetLastError();
