@@ -2,8 +2,9 @@
 
 Both the oracle and the CUDA path consume these per-node coefficients, so a
 mistake in them would be shared by both sides of every parity test; they are
-pinned here against what the tube problem itself fixes (SURVEY reading c10:
-zero-mean oscillating pressure gradient, velocity u(r, t) = Re{c(r) e^{i w t}}):
+pinned here against what the tube problem itself fixes (the reading of the
+workload's Womersley inlet: zero-mean oscillating pressure gradient, velocity
+u(r, t) = Re{c(r) e^{i w t}}):
 
 * c solves the oscillatory tube equation  i w c = G + nu (c'' + c'/r)  for one
   constant G: nu (c'' + c'/r) - i w c, by central finite differences of the
