@@ -5,7 +5,7 @@
  * vessel (R_p, C, R_d, E_max, E_min, beat period) to a periodic-state
  * initialisation of the coupled solver.  The paper has no counterpart: the
  * network only chooses the initial state; the solver of include/lbm.h is run
- * from it unchanged and judges the result.
+ * from it unchanged and decides the result.
  *
  * Conventions: every call returns an lbm_status (include/lbm.h); host arrays
  * are FP32 and copied; nothing is retained.  Flat parameter layout (shared

@@ -17,7 +17,7 @@ status word).
 
 For each reduced precision the waveforms of the last beat are compared with
 the FP32 run's (same metric: max over boundaries and waveforms of
-max_t |W_p - W_FP32| / max_t |W_FP32|), the plain FP32 method being the judge.
+max_t |W_p - W_FP32| / max_t |W_FP32|), the plain FP32 method being the reference.
 
     python -m paper_2112_05258_gb300.aorta_run --beats 10 --out aorta_run.json
 """

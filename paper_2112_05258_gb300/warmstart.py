@@ -19,7 +19,7 @@ prepares features and labels and lays out the predicted fields):
    field (pressure linear along the tube between the two layer pressures,
    axial velocity interpolated linearly between the two mode profiles).
 
-The cold-started method is both the fallback and the judge: warm and cold
+The cold-started method is both the fallback and the reference: warm and cold
 runs are compared on the cycles each needs to become periodic and on the
 periodic waveforms they reach.
 """
@@ -304,7 +304,7 @@ def _evaluate_batch(insts, params, predict, precision_warm, max_cycles, log):
         log(f"{name}: steps {steps}, wall {wall:.2f} s, median cycles "
             f"{float(np.median(cycles[ok])) if ok.any() else None}, unconverged {int((~ok).sum())}")
         lat.close()
-    # the cold method judges the periodic state reached from the warm start
+    # the periodic state reached from the warm start, against the cold one
     for name in ("warm_f32", "warm_" + precision_warm):
         errs = []
         for q in range(len(insts)):

@@ -2,7 +2,7 @@
 short beats, small tubes).  The network is trained on periodic states the
 batched solver produced; on held-out parameter sets the warm-started runs
 must become periodic in fewer beats than cold starts, and reach the same
-periodic waveforms (the cold method is the judge)."""
+periodic waveforms (the cold method is the reference)."""
 import numpy as np
 import pytest
 
