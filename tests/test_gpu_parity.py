@@ -76,6 +76,14 @@ def test_f64_rigid_tube_womersley_rcr(Lattice):
     assert_same(lat, o, inst)
 
 
+def test_f64_lv_tube_along_x(Lattice):
+    # the 0D boundaries on x: every row of the vessel begins and ends with a
+    # boundary node, and the extrapolation links run along the rows
+    inst = configs.lv_tube_x(30)
+    f0 = configs.random_populations(inst, seed=11)
+    assert_same(run_gpu(Lattice, inst, 300, f0=f0), run_oracle(inst, 300, f0=f0), inst)
+
+
 def test_f64_pressure_tube(Lattice):
     inst = configs.pressure_tube(14, 14, 20, 4.5, 0.9, 2e-3, -1e-3)
     lat = run_gpu(Lattice, inst, 200)

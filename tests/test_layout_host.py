@@ -40,7 +40,7 @@ def test_aorta_layout(check):
 
 
 def test_batch_sizes_add_up(check):
-    insts = [configs.lv_tube(), configs.rigid_tube(16, 16, 24, radius=5.0, period=200)]
+    insts = [configs.lv_tube(), configs.rigid_tube(16, 16, 24, radius=5.0, period=200), configs.lv_tube_x(31)]
     st = check(insts)
     assert st["band_cells"] == 0 and st["ib_nodes"] == 0 and st["slabs"] == 0
     assert st["fluid_cells"] == sum(i.n_fluid for i in insts)

@@ -86,6 +86,19 @@ def lv_tube(nx: int = 14, ny: int = 14, nz: int = 32, radius: float = 5.0,
     return inst
 
 
+def lv_tube_x(nx: int = 30, ny: int = 12, nz: int = 12, radius: float = 4.3,
+              tau: float = 0.8, period: int = 300) -> Instance:
+    """The LV tube of :func:`lv_tube` laid along x: inlet plane x = 0, outlet
+    plane x = nx - 1, so that every lattice row of the vessel begins and ends
+    with a 0D boundary node."""
+    z = lv_tube(nx=ny, ny=nz, nz=nx, radius=radius, tau=tau, period=period)
+    node = np.ascontiguousarray(z.node.transpose(2, 1, 0))
+    inst = Instance(node=node, tau=tau, name=f"lv_tube_x_{nx}x{ny}x{nz}_R{radius:g}_T{period}")
+    inst.boundaries.append(lv_boundary(period=period, kappa=LV_KAPPA * 4000.0 / period, axis=0, sign=+1))
+    inst.boundaries.append(Boundary(BC_RCR, 0, -1, list(z.boundaries[1].params)))
+    return inst
+
+
 def pressure_tube(nx: int, ny: int, nz: int, radius: float, tau: float,
                   p_in: float, p_out: float) -> Instance:
     """Tube driven by two constant-pressure ends (NEE pressure coupling)."""
