@@ -234,7 +234,10 @@ lbm_status lbm_read_0d_state_async(lbm_handle *h, int inst, double *out);
 lbm_status lbm_read_waveforms(lbm_handle *h, int inst, double *out, int64_t max_rows, int64_t *rows);
 
 /* Wall-node arrays of instance inst (n_ib x 3 doubles each; NULL to skip):
- * position X, velocity V_s, force on the fluid F, interpolated V_f. */
+ * position X, velocity V_s, force on the fluid F, interpolated V_f.  With
+ * FP64 storage the node state is FP64; with FP32, FP16 or BF16 storage it is
+ * FP32 and the device keeps the displacement X - X0 (rounding ~6e-8 cells at
+ * displacements below one cell), which these calls convert from and to. */
 lbm_status lbm_read_ib(lbm_handle *h, int inst, double *X, double *Vs, double *F, double *Vf);
 lbm_status lbm_set_ib_state(lbm_handle *h, int inst, const double *X, const double *Vs);
 

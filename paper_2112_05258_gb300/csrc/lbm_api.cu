@@ -52,8 +52,10 @@ struct lbm_handle {
     BcStepResult *bc_result = nullptr;
     int32_t *red_bc = nullptr, *red_chunk = nullptr, *app_bc = nullptr, *app_chunk = nullptr;
     int32_t *band = nullptr, *node_inst = nullptr;
-    double *ibX = nullptr, *ibVs = nullptr, *ibI = nullptr, *ibF = nullptr, *ibVf = nullptr;
+    double *ibX = nullptr, *ibVs = nullptr, *ibI = nullptr, *ibF = nullptr, *ibVf = nullptr;  // FP64 storage
+    float *ibD32 = nullptr, *ibVs32 = nullptr, *ibI32 = nullptr, *ibF32 = nullptr, *ibVf32 = nullptr;  // otherwise
     double *ibX0 = nullptr, *ibdA = nullptr, *ibks = nullptr;
+    float *ibg0 = nullptr, *ibdA32 = nullptr, *ibks32 = nullptr;
     uint8_t *ibpin = nullptr;
     int32_t *iblines = nullptr, *ibref = nullptr;
     int32_t *fil_nodes = nullptr, *fil_start = nullptr, *fil_count = nullptr;
@@ -490,10 +492,19 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
         for (size_t q = 0; q < L.inst.size(); q++)
             for (int s = 0; s < L.inst[q].n_ib; s++) ni.push_back((int32_t)q);
         std::vector<double> zero(3 * ns, 0.0);
+        std::vector<float> zero32(3 * ns, 0.0f);
+        std::vector<float> dA32(L.ib_dA.begin(), L.ib_dA.end()), ks32(L.ib_ks.begin(), L.ib_ks.end());
+        // the node state in the arithmetic's precision (FP32: displacements from X0)
+        const bool st64 = h->prec == LBM_F64;
         ok = ck(upload(h, &h->band, L.band), "band") && ck(upload(h, &h->node_inst, ni), "ib") &&
-             ck(upload(h, &h->ibX, L.ib_X0), "ib") && ck(upload(h, &h->ibX0, L.ib_X0), "ib") &&
-             ck(upload(h, &h->ibVs, zero), "ib") && ck(upload(h, &h->ibI, zero), "ib") &&
-             ck(upload(h, &h->ibF, zero), "ib") && ck(upload(h, &h->ibVf, zero), "ib") &&
+             (st64 ? ck(upload(h, &h->ibX, L.ib_X0), "ib") && ck(upload(h, &h->ibVs, zero), "ib") &&
+                         ck(upload(h, &h->ibI, zero), "ib") && ck(upload(h, &h->ibF, zero), "ib") &&
+                         ck(upload(h, &h->ibVf, zero), "ib")
+                   : ck(upload(h, &h->ibD32, zero32), "ib") && ck(upload(h, &h->ibVs32, zero32), "ib") &&
+                         ck(upload(h, &h->ibI32, zero32), "ib") && ck(upload(h, &h->ibF32, zero32), "ib") &&
+                         ck(upload(h, &h->ibVf32, zero32), "ib") && ck(upload(h, &h->ibg0, L.ib_g0), "ib") &&
+                         ck(upload(h, &h->ibdA32, dA32), "ib") && ck(upload(h, &h->ibks32, ks32), "ib")) &&
+             ck(upload(h, &h->ibX0, L.ib_X0), "ib") &&
              ck(upload(h, &h->ibdA, L.ib_dA), "ib") && ck(upload(h, &h->ibks, L.ib_ks), "ib") &&
              ck(upload(h, &h->ibpin, L.ib_pinned), "ib") && ck(upload(h, &h->iblines, L.ib_lines), "ib") &&
              ck(upload(h, &h->ibmask, L.ib_mask), "ib") && ck(upload(h, &h->ibref, L.ib_ref), "ib") &&
@@ -570,6 +581,14 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
     h->ibp.I = h->ibI;
     h->ibp.F = h->ibF;
     h->ibp.Vf = h->ibVf;
+    h->ibp.D32 = h->ibD32;
+    h->ibp.Vs32 = h->ibVs32;
+    h->ibp.I32 = h->ibI32;
+    h->ibp.F32 = h->ibF32;
+    h->ibp.Vf32 = h->ibVf32;
+    h->ibp.g0 = h->ibg0;
+    h->ibp.dA32 = h->ibdA32;
+    h->ibp.ks32 = h->ibks32;
     h->ibp.X0 = h->ibX0;
     h->ibp.dA = h->ibdA;
     h->ibp.ks = h->ibks;
@@ -831,12 +850,22 @@ lbm_status lbm_read_ib(lbm_handle *h, int inst, double *X, double *Vs, double *F
     const InstParam &ip = h->L.inst[inst];
     CK(h, cudaSetDevice(h->device));
     CK(h, cudaStreamSynchronize(h->stream));
-    double *src[4] = {h->ibX, h->ibVs, h->ibF, h->ibVf};
     double *dst[4] = {X, Vs, F, Vf};
-    for (int k = 0; k < 4; k++)
-        if (dst[k] && ip.n_ib)
-            CK(h, cudaMemcpy(dst[k], src[k] + 3 * (size_t)ip.ib_off, 3 * (size_t)ip.n_ib * sizeof(double),
-                             cudaMemcpyDeviceToHost));
+    const size_t m = 3 * (size_t)ip.n_ib, o = 3 * (size_t)ip.ib_off;
+    if (h->prec == LBM_F64) {
+        double *src[4] = {h->ibX, h->ibVs, h->ibF, h->ibVf};
+        for (int k = 0; k < 4; k++)
+            if (dst[k] && m) CK(h, cudaMemcpy(dst[k], src[k] + o, m * sizeof(double), cudaMemcpyDeviceToHost));
+        return LBM_OK;
+    }
+    // FP32 node state; positions are X0 + D
+    float *src[4] = {h->ibD32, h->ibVs32, h->ibF32, h->ibVf32};
+    std::vector<float> tmp(m);
+    for (int k = 0; k < 4; k++) {
+        if (!dst[k] || !m) continue;
+        CK(h, cudaMemcpy(tmp.data(), src[k] + o, m * sizeof(float), cudaMemcpyDeviceToHost));
+        for (size_t j = 0; j < m; j++) dst[k][j] = (k == 0 ? h->L.ib_X0[o + j] : 0.0) + (double)tmp[j];
+    }
     return LBM_OK;
 }
 
@@ -847,9 +876,18 @@ lbm_status lbm_set_ib_state(lbm_handle *h, int inst, const double *X, const doub
         if (!std::isfinite(X[s]) || !std::isfinite(Vs[s])) return fail(h, LBM_ERR_ARG, "non-finite wall state");
     CK(h, cudaSetDevice(h->device));
     CK(h, cudaStreamSynchronize(h->stream));
-    if (ip.n_ib) {
-        CK(h, cudaMemcpy(h->ibX + 3 * (size_t)ip.ib_off, X, 3 * (size_t)ip.n_ib * sizeof(double), cudaMemcpyHostToDevice));
-        CK(h, cudaMemcpy(h->ibVs + 3 * (size_t)ip.ib_off, Vs, 3 * (size_t)ip.n_ib * sizeof(double), cudaMemcpyHostToDevice));
+    const size_t m = 3 * (size_t)ip.n_ib, o = 3 * (size_t)ip.ib_off;
+    if (m && h->prec == LBM_F64) {
+        CK(h, cudaMemcpy(h->ibX + o, X, m * sizeof(double), cudaMemcpyHostToDevice));
+        CK(h, cudaMemcpy(h->ibVs + o, Vs, m * sizeof(double), cudaMemcpyHostToDevice));
+    } else if (m) {  // FP32 node state: displacements from X0
+        std::vector<float> D(m), V(m);
+        for (size_t j = 0; j < m; j++) {
+            D[j] = (float)(X[j] - h->L.ib_X0[o + j]);
+            V[j] = (float)Vs[j];
+        }
+        CK(h, cudaMemcpy(h->ibD32 + o, D.data(), m * sizeof(float), cudaMemcpyHostToDevice));
+        CK(h, cudaMemcpy(h->ibVs32 + o, V.data(), m * sizeof(float), cudaMemcpyHostToDevice));
     }
     return LBM_OK;
 }
@@ -948,8 +986,13 @@ std::vector<CkptSection> ckpt_sections(lbm_handle *h) {
         {h->status, sizeof(unsigned)},
     };
     if (ns) {
-        double *ib[5] = {h->ibX, h->ibVs, h->ibI, h->ibF, h->ibVf};
-        for (double *a : ib) v.push_back({a, 3 * ns * sizeof(double)});
+        if (h->prec == LBM_F64) {
+            double *ib[5] = {h->ibX, h->ibVs, h->ibI, h->ibF, h->ibVf};
+            for (double *a : ib) v.push_back({a, 3 * ns * sizeof(double)});
+        } else {
+            float *ib[5] = {h->ibD32, h->ibVs32, h->ibI32, h->ibF32, h->ibVf32};
+            for (float *a : ib) v.push_back({a, 3 * ns * sizeof(float)});
+        }
     }
     return v;
 }

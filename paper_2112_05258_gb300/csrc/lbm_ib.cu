@@ -10,7 +10,11 @@
 //                   support cells of the 4-point cosine delta, penalty
 //                   integral and force F = alpha I + beta (V_f - V_s) on the
 //                   fluid, spreading of F delta dA with one vector atomic per
-//                   cell, spring update.
+//                   cell, spring update.  With FP32 arithmetic (FP32, FP16 or
+//                   BF16 storage) the node state is FP32 and the position is
+//                   kept as the displacement D = X - X0 (|D| < 1 cell, so its
+//                   rounding is ~6e-8 cells where X itself would round to
+//                   ~6e-5 at x ~ 1000); FP64 storage keeps the FP64 state.
 //   k_filament      one CTA per filament of wall nodes: SGFD tension and
 //                   bending forces (Section 2.3.2) at X(t_n) from shared
 //                   memory, then the wall update of its interior nodes.
@@ -97,12 +101,20 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib, int k
     const int kk = k0 + gt / TPN, q = gt % TPN;
     if (kk >= k1) return;  // the lanes of a node leave together
     const int s = ib.order ? ib.order[kk] : kk;
+    constexpr bool F32 = sizeof(R) == 4;  // FP32 node state (displacements)
     if (q == 0) {  // lane 0 reads the node state after the gathers: bring it towards L2 meanwhile
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.Vs + 3 * s));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.I + 3 * s));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.X0 + 3 * s));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.ks + s));
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.dA + s));
+        if (F32) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.Vs32 + 3 * s));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.I32 + 3 * s));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.ks32 + s));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.dA32 + s));
+        } else {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.Vs + 3 * s));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.I + 3 * s));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.X0 + 3 * s));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.ks + s));
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.dA + s));
+        }
         asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.pinned + s));
     }
     // the support-line table (36 entries) and the fluid mask are read once
@@ -110,30 +122,40 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib, int k
     asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.lines + 36 * (size_t)s + (36 / TPN) * q));
     if (q == 0) asm volatile("prefetch.global.L2 [%0];" ::"l"(ib.mask + 4 * (size_t)s));
     const InstParam &ip = ib.inst[ib.node_inst[s]];
+    // X - 1/2 = i0 + th with th in [0, 1): i0 = ref + d, where d is the cell
+    // offset from the reference cell ref = floor(X0 - 1/2)
     double X[3];
-    int i0[3];
+    float D[3];
+    int i0[3], d[3];
     R w[3][4];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        X[a] = ib.X[3 * s + a];
-        const double h = X[a] - 0.5;
-        const double fl0 = floor(h);
-        i0[a] = (int)fl0;
+        R th;
+        if (F32) {
+            D[a] = ib.D32[3 * s + a];
+            const float t = ib.g0[3 * s + a] + D[a];  // X - 1/2 - ref
+            const float ft = floorf(t);
+            d[a] = (int)ft;
+            th = (R)(t - ft);
+        } else {
+            X[a] = ib.X[3 * s + a];
+            const double h = X[a] - 0.5;
+            const double fl0 = floor(h);
+            d[a] = (int)fl0 - ib.ref[3 * s + a];
+            th = (R)(h - fl0);
+        }
+        i0[a] = ib.ref[3 * s + a] + d[a];
         R Sn, Cs;
-        sincospi_half((R)(h - fl0), &Sn, &Cs);
+        sincospi_half(th, &Sn, &Cs);
 #pragma unroll
         for (int k = 0; k < 4; k++) w[a][k] = delta_weight<R>(Sn, Cs, k);
     }
     // support cells through the node's precomputed line table and fluid mask
     // (box of 6^3 cells around its reference cell; the node may move by less
     // than one cell from it, else the status word reports it)
-    int d[3];
     bool out_of_band = false;
 #pragma unroll
-    for (int a = 0; a < 3; a++) {
-        d[a] = i0[a] - ib.ref[3 * s + a];
-        out_of_band |= (d[a] < -1 || d[a] > 1);
-    }
+    for (int a = 0; a < 3; a++) out_of_band |= (d[a] < -1 || d[a] > 1);
     const V *vb = static_cast<const V *>(ib.vband);
     R vx = 0, vy = 0, vz = 0;
     int lb[4 * PL];
@@ -181,26 +203,46 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib, int k
             vz += __shfl_xor_sync(grp, vz, o, TPN);
         }
     }
-    // the penalty force (FP64) on lane 0 of the node's group, which then
-    // hands F dA to the other lanes for their planes of the spreading
+    // the penalty force on lane 0 of the node's group (in the node state's
+    // precision), which then hands F dA to the other lanes for their planes
+    // of the spreading
     double F[3], Vs[3];
+    float F32v[3], Vs32v[3];
     R Fx = 0, Fy = 0, Fz = 0;
     if (q == 0) {
-        const double Vf[3] = {(double)vx, (double)vy, (double)vz};
+        if (F32) {
+            const float Vf[3] = {(float)vx, (float)vy, (float)vz};
 #pragma unroll
-        for (int a = 0; a < 3; a++) {
-            Vs[a] = ib.Vs[3 * s + a];
-            const double dv = Vf[a] - Vs[a];
-            const double I = ib.I[3 * s + a] + dv;
-            F[a] = ip.alpha * I + ip.beta * dv;
-            ib.I[3 * s + a] = I;
-            ib.F[3 * s + a] = F[a];
-            ib.Vf[3 * s + a] = Vf[a];
+            for (int a = 0; a < 3; a++) {
+                Vs32v[a] = ib.Vs32[3 * s + a];
+                const float dv = Vf[a] - Vs32v[a];
+                const float I = ib.I32[3 * s + a] + dv;
+                F32v[a] = ip.alpha_f * I + ip.beta_f * dv;
+                ib.I32[3 * s + a] = I;
+                ib.F32[3 * s + a] = F32v[a];
+                ib.Vf32[3 * s + a] = Vf[a];
+            }
+            const R dA = (R)ib.dA32[s];
+            Fx = (R)F32v[0] * dA;
+            Fy = (R)F32v[1] * dA;
+            Fz = (R)F32v[2] * dA;
+        } else {
+            const double Vf[3] = {(double)vx, (double)vy, (double)vz};
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                Vs[a] = ib.Vs[3 * s + a];
+                const double dv = Vf[a] - Vs[a];
+                const double I = ib.I[3 * s + a] + dv;
+                F[a] = ip.alpha * I + ip.beta * dv;
+                ib.I[3 * s + a] = I;
+                ib.F[3 * s + a] = F[a];
+                ib.Vf[3 * s + a] = Vf[a];
+            }
+            const R dA = (R)ib.dA[s];
+            Fx = (R)F[0] * dA;
+            Fy = (R)F[1] * dA;
+            Fz = (R)F[2] * dA;
         }
-        const R dA = (R)ib.dA[s];
-        Fx = (R)F[0] * dA;
-        Fy = (R)F[1] * dA;
-        Fz = (R)F[2] * dA;
     }
     if (TPN > 1) {
         Fx = __shfl_sync(grp, Fx, 0, TPN);
@@ -224,13 +266,24 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib, int k
         vec_atomic_add(&b[c], add);
     }
     if (q == 0 && ib.pinned[s] == 0) {  // pinned nodes stay; filament nodes move in k_filament
-        const double inv_ms = ip.inv_ms;
+        if (F32) {
+            const float ks = ib.ks32[s];
 #pragma unroll
-        for (int a = 0; a < 3; a++) {
-            const double acc = (-ib.ks[s] * (X[a] - ib.X0[3 * s + a]) - F[a]) * inv_ms;
-            const double v = Vs[a] + acc;
-            ib.Vs[3 * s + a] = v;
-            ib.X[3 * s + a] = X[a] + v;
+            for (int a = 0; a < 3; a++) {
+                const float acc = (-ks * D[a] - F32v[a]) * ip.inv_ms_f;
+                const float v = Vs32v[a] + acc;
+                ib.Vs32[3 * s + a] = v;
+                ib.D32[3 * s + a] = D[a] + v;
+            }
+        } else {
+            const double inv_ms = ip.inv_ms;
+#pragma unroll
+            for (int a = 0; a < 3; a++) {
+                const double acc = (-ib.ks[s] * (X[a] - ib.X0[3 * s + a]) - F[a]) * inv_ms;
+                const double v = Vs[a] + acc;
+                ib.Vs[3 * s + a] = v;
+                ib.X[3 * s + a] = X[a] + v;
+            }
         }
     }
 }
@@ -252,6 +305,7 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib, int k
 // node and segment in shared memory (one square root per segment).
 constexpr int FIL_THREADS = 512;
 
+template <bool F32>
 __global__ void __launch_bounds__(FIL_THREADS) k_filament(KParams p, IbKParams ib) {
     extern __shared__ double sm[];
     const int k = blockIdx.x;
@@ -264,7 +318,8 @@ __global__ void __launch_bounds__(FIL_THREADS) k_filament(KParams p, IbKParams i
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const int s = ib.fil_nodes[st + i];
 #pragma unroll
-        for (int a = 0; a < 3; a++) P[3 * (i + 1) + a] = ib.X[3 * s + a];
+        for (int a = 0; a < 3; a++)
+            P[3 * (i + 1) + a] = F32 ? ib.X0[3 * s + a] + (double)ib.D32[3 * s + a] : ib.X[3 * s + a];
     }
     __syncthreads();
     if (threadIdx.x < 3) {
@@ -299,10 +354,17 @@ __global__ void __launch_bounds__(FIL_THREADS) k_filament(KParams p, IbKParams i
             const double xa = P[3 * (i + 1) + a];
             const double ff = (TD[3 * i + a] - TD[3 * (i - 1) + a]) * inv_ds -
                               EI * (K[3 * (i + 1) + a] - 2.0 * K[3 * i + a] + K[3 * (i - 1) + a]) * inv_ds2;
-            const double acc = (-ib.ks[s] * (xa - ib.X0[3 * s + a]) + ff - ib.F[3 * s + a]) * inv_ms;
-            const double v = ib.Vs[3 * s + a] + acc;
-            ib.Vs[3 * s + a] = v;
-            ib.X[3 * s + a] = xa + v;
+            const double Fp = F32 ? (double)ib.F32[3 * s + a] : ib.F[3 * s + a];
+            const double acc = (-ib.ks[s] * (xa - ib.X0[3 * s + a]) + ff - Fp) * inv_ms;
+            if (F32) {
+                const double v = (double)ib.Vs32[3 * s + a] + acc;
+                ib.Vs32[3 * s + a] = (float)v;
+                ib.D32[3 * s + a] = (float)((xa - ib.X0[3 * s + a]) + v);
+            } else {
+                const double v = ib.Vs[3 * s + a] + acc;
+                ib.Vs[3 * s + a] = v;
+                ib.X[3 * s + a] = xa + v;
+            }
         }
     }
 }
@@ -310,7 +372,12 @@ __global__ void __launch_bounds__(FIL_THREADS) k_filament(KParams p, IbKParams i
 static size_t filament_smem(int max_fil) { return (size_t)(9 * max_fil + 6) * sizeof(double); }
 
 cudaError_t prepare_filament_kernel(int max_fil) {
-    return cudaFuncSetAttribute(k_filament, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)filament_smem(max_fil));
+    cudaError_t e = cudaFuncSetAttribute(k_filament<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)filament_smem(max_fil));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_filament<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)filament_smem(max_fil));
+    return e;
 }
 
 template <class S> static void launch_nodes(const KParams &p, const IbKParams &ib, int k0, int k1, cudaStream_t st) {
@@ -341,7 +408,10 @@ cudaError_t launch_ib(int prec, const void *fin, const KParams &p, const IbKPara
     cudaError_t e = launch_band_moments(prec, fin, p, ib, 0, ib.n_band, st);
     if (e == cudaSuccess) e = launch_ib_nodes(prec, p, ib, 0, ib.n_nodes, st);
     if (e == cudaSuccess && ib.n_fil) {
-        k_filament<<<ib.n_fil, FIL_THREADS, filament_smem(ib.max_fil), st>>>(p, ib);
+        if (prec == 3)
+            k_filament<false><<<ib.n_fil, FIL_THREADS, filament_smem(ib.max_fil), st>>>(p, ib);
+        else
+            k_filament<true><<<ib.n_fil, FIL_THREADS, filament_smem(ib.max_fil), st>>>(p, ib);
         e = cudaGetLastError();
     }
     return e;

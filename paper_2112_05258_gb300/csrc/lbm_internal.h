@@ -80,6 +80,7 @@ struct InstParam {
     int bc_first, n_bc;
     double alpha, beta, ms;
     double inv_ms;  // 1/ms (FP64 division is slow on the device)
+    float alpha_f, beta_f, inv_ms_f;  // the same rounded to FP32 (wall-node state in FP32)
 };
 
 enum { BC_VELOCITY = 0, BC_RCR = 1, BC_LV = 2, BC_PRESSURE = 3 };
@@ -135,6 +136,7 @@ struct Layout {
     std::vector<int32_t> ib_lines;
     std::vector<uint64_t> ib_mask;
     std::vector<int32_t> ib_ref;        // i0 per node (3 ints)
+    std::vector<float> ib_g0;           // X0 - 1/2 - i0 per node (3, in [0, 1)), rounded to FP32
     std::vector<double> ib_X0, ib_dA, ib_ks;
     std::vector<uint8_t> ib_pinned;     // 0 spring, 1 pinned, 2 moved by its filament
     // filaments: global wall-node lists, first entry and count per filament, (ds, Eh, EI)

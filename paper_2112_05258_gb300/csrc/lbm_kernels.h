@@ -72,8 +72,12 @@ struct IbKParams {
     const int32_t *node_inst;   // per node
     const InstParam *inst;
     const int32_t *rowid;
-    double *X, *Vs, *I, *F, *Vf;  // 3 per node
+    // wall-node state, 3 per node: FP64 with FP64 storage (X, V_s, I, F, V_f);
+    // FP32 otherwise, with the position as the displacement D = X - X0
+    double *X, *Vs, *I, *F, *Vf;
+    float *D32, *Vs32, *I32, *F32, *Vf32;
     const double *X0, *dA, *ks;
+    const float *g0, *dA32, *ks32;  // X0 - 1/2 - ref (3 per node), dA, k_s in FP32
     const uint8_t *pinned;
     void *vband;                // fluid velocity j + b/2 (previous step's b) at band cells, 4 x compute type per cell
     int threads_per_node;       // 1, 2 or 4 threads of the node kernel per wall node

@@ -47,6 +47,9 @@ std::string build_layout(const lbm_config *cfg, Layout &L) {
         ip.beta = d.ib_beta;
         ip.ms = d.ib_ms;
         ip.inv_ms = d.ib_ms > 0 ? 1.0 / d.ib_ms : 0.0;
+        ip.alpha_f = (float)ip.alpha;
+        ip.beta_f = (float)ip.beta;
+        ip.inv_ms_f = (float)ip.inv_ms;
         L.n_box += nbox;
         L.inst_cell_begin[q] = cell;
         const int row_base = (int)L.rows.size();
@@ -289,6 +292,7 @@ std::string build_layout(const lbm_config *cfg, Layout &L) {
             int i0[3];
             for (int a = 0; a < 3; a++) i0[a] = (int)std::floor(d.ib_X0[3 * s + a] - 0.5);
             for (int a = 0; a < 3; a++) L.ib_ref.push_back(i0[a]);
+            for (int a = 0; a < 3; a++) L.ib_g0.push_back((float)((d.ib_X0[3 * s + a] - 0.5) - i0[a]));
             uint64_t mask[4] = {0, 0, 0, 0};
             for (int jz = 0; jz < 6; jz++)
                 for (int jy = 0; jy < 6; jy++) {
