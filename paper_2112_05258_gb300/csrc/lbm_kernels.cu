@@ -164,9 +164,36 @@ __global__ void __launch_bounds__(BC_CHUNK) k_bc_apply(S *__restrict__ f, KParam
     const size_t N = (size_t)p.n;
     const R *aux = static_cast<const R *>(p.aux);
     const int L = ch * BC_CHUNK + threadIdx.x;
+    const bool have = L < P.n_links;
+    if (!STEP_HERE && !have) return;
+    // the link's inputs, read before the 0D step's result is known (with
+    // STEP_HERE they arrive while one thread takes the step): x_b, x_f and i,
+    // the forced velocity, sum s and f*_i at x_f, and the closure velocity or
+    // the inlet profile of the link's node
+    int cb = 0, cf = 0, i = 0;
+    R vf[3] = {R(0), R(0), R(0)}, sdf = R(0), post = R(0);
+    double pr[3] = {0.0, 0.0, 0.0}, v0o[3] = {0.0, 0.0, 0.0};
+    if (have) {
+        cb = q.lk_xb[P.link_off + L];
+        cf = q.lk_xf[P.link_off + L];
+        i = q.lk_i[P.link_off + L];
+        forced_velocity<R>(p, cf, vf);
+        sdf = aux[cf];
+        post = Storage<S>::ld(f + pidx(i, (uint32_t)cf, (uint32_t)N));
+        if (P.kind == BC_VELOCITY) {
+            const double *prof = q.profile + 3 * (size_t)(P.node_off + q.lk_node[P.link_off + L]);
+            pr[0] = prof[0];
+            pr[1] = prof[1];
+            pr[2] = prof[2];
+        } else if (P.kind == BC_LV) {  // v_0(T_d) of an earlier closure (rewritten below if one happens now)
+            const double *v0 = q.v0 + 3 * (size_t)(P.xf_off + q.lk_xfi[P.link_off + L]);
+            v0o[0] = v0[0];
+            v0o[1] = v0[1];
+            v0o[2] = v0[2];
+        }
+    }
     BcStepResult r;
     if (!STEP_HERE) {
-        if (L >= P.n_links) return;
         r = q.result[b];
     } else {
         __shared__ BcStepResult s_r;
@@ -176,17 +203,12 @@ __global__ void __launch_bounds__(BC_CHUNK) k_bc_apply(S *__restrict__ f, KParam
             if (threadIdx.x == 0) s_r = bc_step(P, b, Q, Ps, *p.step, q, ch == 0);
         }
         __syncthreads();
-        if (L >= P.n_links) return;
+        if (!have) return;
         r = s_r;
     }
-    const int cb = q.lk_xb[P.link_off + L];
-    const int cf = q.lk_xf[P.link_off + L];
-    const int i = q.lk_i[P.link_off + L];
-    R vf[3];
-    forced_velocity<R>(p, cf, vf);
     R dP, vs[3];  // P* - P(x_f) and v*
     if (r.ptype) {  // pressure-type: (P_0D(t_{n+1}), v(x_f, t_n))
-        dP = (R)r.Pg - aux[cf] / R(3);
+        dP = (R)r.Pg - sdf / R(3);
         vs[0] = vf[0];
         vs[1] = vf[1];
         vs[2] = vf[2];
@@ -194,12 +216,11 @@ __global__ void __launch_bounds__(BC_CHUNK) k_bc_apply(S *__restrict__ f, KParam
         dP = R(0);
         vs[0] = vs[1] = vs[2] = R(0);
         if (P.kind == BC_VELOCITY) {
-            const double *pr = q.profile + 3 * (size_t)(P.node_off + q.lk_node[P.link_off + L]);
             vs[P.axis] = (R)((double)P.sign * (pr[0] + pr[1] * r.cosp - pr[2] * r.sinp));
         } else if (P.kind == BC_LV) {  // closed valve: v_0(T_d) S(t, T_d, N_S)
-            double *v0 = q.v0 + 3 * (size_t)(P.xf_off + q.lk_xfi[P.link_off + L]);
             R u0[3];
             if (r.closed) {  // v_0(T_d) = v(x_f, T_d); links sharing x_f store the same value
+                double *v0 = q.v0 + 3 * (size_t)(P.xf_off + q.lk_xfi[P.link_off + L]);
 #pragma unroll
                 for (int a = 0; a < 3; a++) {
                     u0[a] = vf[a];
@@ -207,7 +228,7 @@ __global__ void __launch_bounds__(BC_CHUNK) k_bc_apply(S *__restrict__ f, KParam
                 }
             } else {
 #pragma unroll
-                for (int a = 0; a < 3; a++) u0[a] = (R)v0[a];
+                for (int a = 0; a < 3; a++) u0[a] = (R)v0o[a];
             }
             const R Sm = (R)r.S;
             vs[0] = u0[0] * Sm;
@@ -222,7 +243,6 @@ __global__ void __launch_bounds__(BC_CHUNK) k_bc_apply(S *__restrict__ f, KParam
     const R us2 = vs[0] * vs[0] + vs[1] * vs[1] + vs[2] * vs[2];
     const R uf2 = vf[0] * vf[0] + vf[1] * vf[1] + vf[2] * vf[2];
     const R dfeq = w * R(3) * dP + w * (R(3) * (eus - euf) + R(4.5) * (eus * eus - euf * euf) - R(1.5) * (us2 - uf2));
-    const R post = Storage<S>::ld(f + pidx(i, (uint32_t)cf, (uint32_t)N));
     Storage<S>::st(f + pidx(i, (uint32_t)cb, (uint32_t)N), post + dfeq);
 }
 
