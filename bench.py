@@ -58,6 +58,7 @@ def parse_args():
                     help="aorta: the full-size elastic-wall case (default); batch: 256 uneven rigid tubes; "
                          "tube: the small 24x24x64 tube the oracle runs in full (latency, not bandwidth)")
     ap.add_argument("--autotune", action="store_true", help="pick block size and occupancy variant first")
+    ap.add_argument("--sc-shape", default="", help="BLOCK,VARIANT: fix the stream-collide launch shape (variant 0..4)")
     ap.add_argument("--ib-tpn", type=int, default=0, help="threads per wall node of the node kernel (0: default 2)")
     ap.add_argument("--ib-slabs", type=int, default=0,
                     help="slabs of the pipelined wall-node step (0 or 1: one launch per kernel, the library's default)")
@@ -266,6 +267,10 @@ def main():
                   ib_slabs=args.ib_slabs, ib_threads_per_node=args.ib_tpn)
     info = lat.info()
     tuned = None
+    if args.sc_shape:
+        blk, var = (int(v) for v in args.sc_shape.split(","))
+        lat.set_stream_collide_shape(blk, var)
+        tuned = {"block": blk, "variant": var}
     if args.autotune:
         tuned = dict(zip(("block", "min_blocks_per_sm", "cells_per_thread"), lat.autotune(iters=10)))
     cells = info.fluid_cells
