@@ -65,6 +65,15 @@ def parse_args():
     return ap.parse_args()
 
 
+def launches(info, steps):
+    """Kernel launches of `steps` steps taken as lbm_step does them: whole step
+    graphs, then single-step graphs for the rest; a graph's first step (and a
+    single step) issues launches_first_step, its later steps launches_per_step."""
+    g = info.graph_steps
+    full, rest = divmod(steps, g)
+    return full * (info.launches_first_step + (g - 1) * info.launches_per_step) + rest * info.launches_first_step
+
+
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -274,7 +283,6 @@ def main():
     if args.autotune:
         tuned = dict(zip(("block", "min_blocks_per_sm", "cells_per_thread"), lat.autotune(iters=10)))
     cells = info.fluid_cells
-    kernels_per_step = info.launches_per_step
 
     def barrier():
         torch.cuda.synchronize()
@@ -361,7 +369,7 @@ def main():
                              "band_cells": info.band_cells,
                              "frac_populations_only": pop_bytes / per_launch_s / 1e9 / peak,
                              "launch_ms": per_launch_s * 1e3, "timed_launches": n_launch},
-                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": kernels_per_step * args.steps,
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches(info, args.steps),
                 "clocks": clk}
         print(json.dumps(line), flush=True)
     lat.close()

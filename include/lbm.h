@@ -152,7 +152,11 @@ typedef struct {
     int precision;
     int bytes_per_population;
     int slabs;             /* slabs of the pipelined step with wall nodes (0: one launch per kernel) */
-    int launches_per_step; /* kernel launches of one step in the step graphs */
+    int launches_per_step; /* kernel launches of a step in the step graphs after the graph's first step
+                              (with wall nodes, the band velocities of such a step were issued as two
+                              launches beside the previous step's 0D boundary kernels) */
+    int launches_first_step; /* kernel launches of a graph's first step and of a single step */
+    int graph_steps;         /* steps per step graph */
 } lbm_info_t;
 
 /* Sizes of the layout lbm_create would build (see lbm_check_config). */

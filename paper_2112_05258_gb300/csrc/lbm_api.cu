@@ -86,6 +86,18 @@ struct lbm_handle {
     cudaStream_t s_node = nullptr, s_sc = nullptr;  // wall-node kernels, stream-collide
     std::vector<cudaEvent_t> ev_bm, ev_node, ev_sc;
     cudaEvent_t ev_fork = nullptr;
+    // Inside the step graphs, the next step's band velocities run beside this
+    // step's 0D boundary kernels: the band entries that are not first-layer
+    // cells (band_ind) read no ghost population and no force density that the
+    // boundary kernels read, so they start as soon as stream-collide ends (low
+    // priority stream s_band); the first-layer band entries (band_dep) follow
+    // the boundary kernels (high priority stream s_bc).  Both join the
+    // caller's stream before the node kernel.
+    bool overlap = false;
+    int32_t *band_ind = nullptr, *band_dep = nullptr;
+    int n_band_ind = 0, n_band_dep = 0;
+    cudaStream_t s_band = nullptr, s_bc = nullptr;
+    cudaEvent_t ev_ofork = nullptr, ev_oband = nullptr, ev_obc = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t graph1[2] = {nullptr, nullptr};  // single steps (by parity), for step counts below graph_steps
     // kernel timing
@@ -251,10 +263,14 @@ lbm_status launch_step_slabs(lbm_handle *h) {
     return LBM_OK;
 }
 
-lbm_status launch_step(lbm_handle *h, bool timed) {
+// One step.  band_done: the band velocities of this step were issued by the
+// previous step (next = true there); next: issue the next step's band
+// velocities beside this step's boundary kernels (graph capture only; the
+// last step of a graph leaves them to the next graph's first step).
+lbm_status launch_step(lbm_handle *h, bool timed, bool band_done = false, bool next = false) {
     if (h->n_slab && !timed) return launch_step_slabs(h);
     void *fin = h->f[h->parity], *fout = h->f[1 - h->parity];
-    if (h->ibp.n_nodes) CK(h, launch_ib(h->prec, fin, h->kp, h->ibp, h->stream));
+    if (h->ibp.n_nodes) CK(h, launch_ib(h->prec, fin, h->kp, h->ibp, h->stream, !band_done));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (timed) {
         if (h->ev_used + 2 > h->ev.size()) {
@@ -280,7 +296,23 @@ lbm_status launch_step(lbm_handle *h, bool timed) {
         CK(h, cudaEventRecord(e1, h->stream));
         h->timed_launches++;
     }
-    CK(h, launch_boundary(h->prec, fout, h->kp, h->bp, h->stream));
+    if (next && h->overlap && !timed) {
+        CK(h, cudaEventRecord(h->ev_ofork, h->stream));
+        CK(h, cudaStreamWaitEvent(h->s_band, h->ev_ofork, 0));
+        CK(h, cudaStreamWaitEvent(h->s_bc, h->ev_ofork, 0));
+        IbKParams ib = h->ibp;
+        ib.band = h->band_ind;
+        CK(h, launch_band_moments(h->prec, fout, h->kp, ib, 0, h->n_band_ind, h->s_band));
+        CK(h, cudaEventRecord(h->ev_oband, h->s_band));
+        CK(h, launch_boundary(h->prec, fout, h->kp, h->bp, h->s_bc));
+        ib.band = h->band_dep;
+        CK(h, launch_band_moments(h->prec, fout, h->kp, ib, 0, h->n_band_dep, h->s_bc));
+        CK(h, cudaEventRecord(h->ev_obc, h->s_bc));
+        CK(h, cudaStreamWaitEvent(h->stream, h->ev_oband, 0));
+        CK(h, cudaStreamWaitEvent(h->stream, h->ev_obc, 0));
+    } else {
+        CK(h, launch_boundary(h->prec, fout, h->kp, h->bp, h->stream));
+    }
     h->parity ^= 1;
     return LBM_OK;
 }
@@ -291,7 +323,8 @@ lbm_status ensure_graph(lbm_handle *h) {
     cudaGraph_t g = nullptr;
     CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
     lbm_status st = LBM_OK;
-    for (int k = 0; k < h->graph_steps && st == LBM_OK; k++) st = launch_step(h, false);
+    for (int k = 0; k < h->graph_steps && st == LBM_OK; k++)
+        st = launch_step(h, false, k > 0 && h->overlap, k + 1 < h->graph_steps && h->overlap);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     h->parity = par;  // capture does not run anything
     if (st != LBM_OK) {
@@ -623,6 +656,25 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
             h->n_slab = K;
             h->ibp.order = h->node_order;
         }
+    }
+    if (ns && !h->n_slab) {
+        // band entries that are first-layer cells of a 0D boundary (their pulls
+        // may read ghosts, and the ghost kernel reads their force density)
+        std::vector<uint8_t> xf((size_t)n, 0);
+        for (int32_t c : L.lk_xf) xf[(size_t)c] = 1;
+        std::vector<int32_t> ind, dep;
+        for (int32_t c : L.band) ((L.flags[(size_t)c] & FL_XF) || xf[(size_t)c] ? dep : ind).push_back(c);
+        int lo = 0, hi = 0;
+        bool sok = ck(upload(h, &h->band_ind, ind), "band") && ck(upload(h, &h->band_dep, dep), "band") &&
+                   ck(cudaDeviceGetStreamPriorityRange(&lo, &hi), "stream priorities") &&
+                   ck(cudaStreamCreateWithPriority(&h->s_band, cudaStreamNonBlocking, lo), "streams") &&
+                   ck(cudaStreamCreateWithPriority(&h->s_bc, cudaStreamNonBlocking, hi), "streams");
+        for (auto *e : {&h->ev_ofork, &h->ev_oband, &h->ev_obc})
+            sok = sok && ck(cudaEventCreateWithFlags(e, cudaEventDisableTiming), "events");
+        if (!sok) return bail(LBM_ERR_CUDA, h->err);
+        h->n_band_ind = (int)ind.size();
+        h->n_band_dep = (int)dep.size();
+        h->overlap = true;
     }
     if (cudaDeviceSynchronize() != cudaSuccess) return bail(LBM_ERR_CUDA, "set-up failed");
     *out = h;
@@ -1175,6 +1227,10 @@ lbm_status lbm_get_info(lbm_handle *h, lbm_info_t *info) {
         n = (L.n_stored > 0) + (L.ib_dA.empty() ? 0 : (L.band.empty() ? 0 : 1) + 1 + (L.fil_start.empty() ? 0 : 1));
     }
     info->launches_per_step = n + (L.bc.empty() ? 0 : 2);
+    info->launches_first_step = info->launches_per_step;
+    if (h->overlap)  // band velocities as the two lists (an empty list launches nothing)
+        info->launches_per_step += (h->n_band_ind > 0) + (h->n_band_dep > 0) - 1;
+    info->graph_steps = h->graph_steps;
     return LBM_OK;
 }
 
@@ -1193,6 +1249,10 @@ void lbm_destroy(lbm_handle *h) {
         for (auto e : *v)
             if (e) cudaEventDestroy(e);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    for (auto e : {h->ev_ofork, h->ev_oband, h->ev_obc})
+        if (e) cudaEventDestroy(e);
+    if (h->s_band) cudaStreamDestroy(h->s_band);
+    if (h->s_bc) cudaStreamDestroy(h->s_bc);
     if (h->s_node) cudaStreamDestroy(h->s_node);
     if (h->s_sc) cudaStreamDestroy(h->s_sc);
     if (h->par_ring) {

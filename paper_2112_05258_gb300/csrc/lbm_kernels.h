@@ -116,7 +116,9 @@ cudaError_t launch_cycle_change(const BcKParams &q, const int *bc_first, const i
                                 long long steps, double *delta, int n_inst, cudaStream_t s);
 cudaError_t launch_init(int prec, void *fout, const KParams &p, const double *f19, int c0, int c1,
                         cudaStream_t s);
-cudaError_t launch_ib(int prec, const void *fin, const KParams &p, const IbKParams &ib, cudaStream_t s);
+// band velocities (unless band = false: issued earlier), node kernel, filaments
+cudaError_t launch_ib(int prec, const void *fin, const KParams &p, const IbKParams &ib, cudaStream_t s,
+                      bool band = true);
 // the band-velocity pass over band-list entries [t0, t1), the node kernel over ib.order[k0 .. k1)
 cudaError_t launch_band_moments(int prec, const void *fin, const KParams &p, const IbKParams &ib, int t0, int t1,
                                 cudaStream_t s);

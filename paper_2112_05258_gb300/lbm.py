@@ -58,7 +58,8 @@ class Info(ctypes.Structure):
                 ("ib_nodes", ctypes.c_int64), ("links", ctypes.c_int64), ("steps", ctypes.c_int64),
                 ("device_bytes", ctypes.c_int64), ("precision", ctypes.c_int),
                 ("bytes_per_population", ctypes.c_int), ("slabs", ctypes.c_int),
-                ("launches_per_step", ctypes.c_int)]
+                ("launches_per_step", ctypes.c_int), ("launches_first_step", ctypes.c_int),
+                ("graph_steps", ctypes.c_int)]
 
 
 class LayoutStats(ctypes.Structure):

@@ -220,9 +220,13 @@ def test_graph_equals_direct_launches(Lattice):
 def test_graph_equals_direct_launches_with_ib(Lattice, filaments):
     # the same kernels captured in graphs or launched one by one: only the
     # order of the spreading atomics may differ
+    # (inside the graphs the band velocities of the next step run beside the
+    # boundary kernels, as two lists: both are non-empty on this tube)
     inst = configs.ib_tube(filaments=filaments)
     for prec, tol in (("f64", 1e-14), ("f32", 1e-6)):
         g = Lattice([inst], precision=prec, graph_steps=8)
+        info = g.info()
+        assert info.graph_steps == 8 and info.launches_per_step == info.launches_first_step + 1
         g.step(203)
         d = Lattice([inst], precision=prec)
         d.set_kernel_timing(True)
