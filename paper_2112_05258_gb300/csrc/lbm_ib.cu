@@ -74,19 +74,7 @@ template <class R> __device__ __forceinline__ R delta_weight(R Sn, R Cs, int k) 
 __device__ __forceinline__ void sincospi_half(float th, float *s, float *c) { sincospif(0.5f * th, s, c); }
 __device__ __forceinline__ void sincospi_half(double th, double *s, double *c) { sincospi(0.5 * th, s, c); }
 
-__device__ __forceinline__ void vec_atomic_add(float4 *a, float4 v) {
-#ifndef EXP_NOATOM
-    atomicAdd(a, v);
-#endif
-}
-#ifndef EXP_LDG
-#define EXP_LDG 0
-#endif
-#ifndef EXP_NB
-#define EXP_NB 128
-#endif
-template <class V> __device__ __forceinline__ V ldv(const V *p) { return *p; }
-template <> __device__ __forceinline__ float4 ldv<float4>(const float4 *p) { return EXP_LDG ? __ldg(p) : *p; }
+__device__ __forceinline__ void vec_atomic_add(float4 *a, float4 v) { atomicAdd(a, v); }
 __device__ __forceinline__ void vec_atomic_add(double4a *a, double4a v) {
     atomicAdd(&a->x, v.x);
     atomicAdd(&a->y, v.y);
@@ -105,7 +93,7 @@ __device__ __forceinline__ void vec_atomic_add(double4a *a, double4a v) {
 // The kernel takes the wall nodes ib.order[k0 .. k1) (all nodes in index
 // order when ib.order is null).
 template <class S, int TPN>
-__global__ void __launch_bounds__(EXP_NB) k_ib_nodes(KParams p, IbKParams ib, int k0, int k1) {
+__global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib, int k0, int k1) {
     using R = typename Storage<S>::R;
     using V = typename Vec4<R>::T;
     constexpr int PL = 4 / TPN;
@@ -196,14 +184,7 @@ __global__ void __launch_bounds__(EXP_NB) k_ib_nodes(KParams p, IbKParams ib, in
                     // branch-free, so that the loads can all be in flight: a
                     // missing cell reads slot 0 (zeroed at creation, finite)
                     // with weight 0
-#ifdef EXP_NOGATHER
-                    V v;
-                    v.x = (R)(base + dx) * R(1e-12);
-                    v.y = v.x;
-                    v.z = v.x;
-#else
-                    const V v = ldv<V>(vb + (ok ? base + i0[0] + dx - 1 : 0));
-#endif
+                    const V v = vb[ok ? base + i0[0] + dx - 1 : 0];
                     const R dd = ok ? w[0][dx] * wyz : R(0);
                     vx += v.x * dd;
                     vy += v.y * dd;
@@ -401,11 +382,11 @@ cudaError_t prepare_filament_kernel(int max_fil) {
 
 template <class S> static void launch_nodes(const KParams &p, const IbKParams &ib, int k0, int k1, cudaStream_t st) {
     const int tpn = ib.threads_per_node;
-    const int grid = (int)(((long long)(k1 - k0) * tpn + EXP_NB - 1) / EXP_NB);
+    const int grid = (int)(((long long)(k1 - k0) * tpn + 127) / 128);
     if (grid == 0) return;
-    if (tpn == 1) k_ib_nodes<S, 1><<<grid, EXP_NB, 0, st>>>(p, ib, k0, k1);
-    else if (tpn == 2) k_ib_nodes<S, 2><<<grid, EXP_NB, 0, st>>>(p, ib, k0, k1);
-    else k_ib_nodes<S, 4><<<grid, EXP_NB, 0, st>>>(p, ib, k0, k1);
+    if (tpn == 1) k_ib_nodes<S, 1><<<grid, 128, 0, st>>>(p, ib, k0, k1);
+    else if (tpn == 2) k_ib_nodes<S, 2><<<grid, 128, 0, st>>>(p, ib, k0, k1);
+    else k_ib_nodes<S, 4><<<grid, 128, 0, st>>>(p, ib, k0, k1);
 }
 
 cudaError_t launch_band_moments(int prec, const void *fin, const KParams &p, const IbKParams &ib, int t0, int t1,
