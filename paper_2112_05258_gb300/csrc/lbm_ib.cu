@@ -92,15 +92,30 @@ __device__ __forceinline__ void vec_atomic_add(double4a *a, double4a v) {
 // compute the same penalty force; lane 0 writes the node state.
 // The kernel takes the wall nodes ib.order[k0 .. k1) (all nodes in index
 // order when ib.order is null).
+//
+// With two threads per node, consecutive nodes (the pair k0 + 2m, k0 + 2m + 1,
+// neighbours on a ring, whose supports share about 70 % of their cells) merge
+// their spreading: the first node of the pair adds the second node's
+// contribution F' delta(x - X') dA' to every cell of its own support that
+// the second support also covers (one vector atomic for both), and the second
+// node spreads only into the cells outside the first one's support.  On the
+// aorta membrane this takes the atomics from 64 to about 42 per node.  The
+// partner's weights, reference cell and force come by shuffles within the
+// pair's four lanes; a pair whose supports do not overlap, or with a node out
+// of its band or past k1, spreads node by node.
 template <class S, int TPN>
 __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib, int k0, int k1) {
     using R = typename Storage<S>::R;
     using V = typename Vec4<R>::T;
     constexpr int PL = 4 / TPN;
+    constexpr bool PAIRED = TPN == 2;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int kk = k0 + gt / TPN, q = gt % TPN;
-    if (kk >= k1) return;  // the lanes of a node leave together
-    const int s = ib.order ? ib.order[kk] : kk;
+    // the lanes of a node leave together; with pairs, those of a pair (a
+    // second node past k1 stays, idle, for the pair's shuffles)
+    if ((PAIRED ? k0 + ((gt / TPN) & ~1) : kk) >= k1) return;
+    const bool dead = kk >= k1;
+    const int s = ib.order ? ib.order[dead ? k1 - 1 : kk] : (dead ? k1 - 1 : kk);
     constexpr bool F32 = sizeof(R) == 4;  // FP32 node state (displacements)
     if (q == 0) {  // lane 0 reads the node state after the gathers: bring it towards L2 meanwhile
         if (F32) {
@@ -193,7 +208,8 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib, int k
             }
         }
     }
-    if (out_of_band) atomicOr(p.status, 2u);
+    if (out_of_band && !dead) atomicOr(p.status, 2u);
+    if (dead) valid = 0;
     const unsigned grp = TPN > 1 ? ((1u << TPN) - 1u) << ((threadIdx.x & 31) & ~(TPN - 1)) : 0u;
     if (TPN > 1) {
 #pragma unroll
@@ -209,7 +225,7 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib, int k
     double F[3], Vs[3];
     float F32v[3], Vs32v[3];
     R Fx = 0, Fy = 0, Fz = 0;
-    if (q == 0) {
+    if (q == 0 && !dead) {
         if (F32) {
             const float Vf[3] = {(float)vx, (float)vy, (float)vz};
 #pragma unroll
@@ -249,12 +265,53 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib, int k
         Fy = __shfl_sync(grp, Fy, 0, TPN);
         Fz = __shfl_sync(grp, Fz, 0, TPN);
     }
+    // pair merge: the partner's offsets e = d - (i0' - i0) of this lane's
+    // support cells d; pw[a][d] = partner weight at e (0 outside [0, 4)), and
+    // pin[a] the bits d with e inside, per axis (z: this lane's planes)
+    bool merge = false, first = true;
+    R pw[3][4], pF[3] = {R(0), R(0), R(0)};
+    uint32_t pin[3] = {0u, 0u, 0u};
+    if (PAIRED) {
+        const unsigned pm = 0xFu << ((threadIdx.x & 31) & ~3u);
+        const bool ok = !dead && !out_of_band;
+        first = ((gt / TPN) & 1) == 0;
+        const bool pok = __shfl_xor_sync(pm, (int)ok, TPN) != 0;
+        int D[3];
+        bool near = true;
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            D[a] = __shfl_xor_sync(pm, i0[a], TPN) - i0[a];
+            near = near && D[a] > -4 && D[a] < 4;
+        }
+        R ow[3][4];
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int k = 0; k < 4; k++) ow[a][k] = __shfl_xor_sync(pm, w[a][k], TPN);
+        pF[0] = __shfl_xor_sync(pm, Fx, TPN);
+        pF[1] = __shfl_xor_sync(pm, Fy, TPN);
+        pF[2] = __shfl_xor_sync(pm, Fz, TPN);
+        merge = ok && pok && near;
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int dd = 0; dd < 4; dd++) {
+                const int e = dd - D[a];
+                R v = R(0);
+#pragma unroll
+                for (int k = 0; k < 4; k++) v = (e == k) ? ow[a][k] : v;
+                pw[a][dd] = v;
+                pin[a] |= (uint32_t)(e >= 0 && e < 4) << dd;
+            }
+    }
     V *b = static_cast<V *>(const_cast<void *>(p.b));
 #pragma unroll
     for (int k = 0; k < 16 * PL; k++) {
         if (!((valid >> k) & 1ull)) continue;
         const int dx = k & 3, dy = (k >> 2) & 3, j = k >> 4;
         const int dz = q * PL + j;
+        // the second node of a merged pair leaves the cells the first one covers
+        if (PAIRED && merge && !first && ((pin[0] >> dx) & (pin[1] >> dy) & (pin[2] >> dz) & 1u)) continue;
         const R wz = w[2][0] * (dz == 0) + w[2][1] * (dz == 1) + w[2][2] * (dz == 2) + w[2][3] * (dz == 3);
         const int c = lb[dy + 4 * j] + i0[0] + dx - 1;
         const R d = w[0][dx] * (w[1][dy] * wz);
@@ -263,9 +320,16 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib, int k
         add.y = Fy * d;
         add.z = Fz * d;
         add.w = 0;
+        if (PAIRED && merge && first) {
+            const R pwz = pw[2][0] * (dz == 0) + pw[2][1] * (dz == 1) + pw[2][2] * (dz == 2) + pw[2][3] * (dz == 3);
+            const R e = pw[0][dx] * (pw[1][dy] * pwz);
+            add.x += pF[0] * e;
+            add.y += pF[1] * e;
+            add.z += pF[2] * e;
+        }
         vec_atomic_add(&b[c], add);
     }
-    if (q == 0 && ib.pinned[s] == 0) {  // pinned nodes stay; filament nodes move in k_filament
+    if (q == 0 && !dead && ib.pinned[s] == 0) {  // pinned nodes stay; filament nodes move in k_filament
         if (F32) {
             const float ks = ib.ks32[s];
 #pragma unroll
