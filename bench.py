@@ -59,7 +59,7 @@ def parse_args():
                          "tube: the small 24x24x64 tube the oracle runs in full (latency, not bandwidth)")
     ap.add_argument("--autotune", action="store_true", help="pick block size and occupancy variant first")
     ap.add_argument("--sc-shape", default="", help="BLOCK,VARIANT: fix the stream-collide launch shape (variant 0..4)")
-    ap.add_argument("--ib-tpn", type=int, default=0, help="threads per wall node of the node kernel (0: default 2)")
+    ap.add_argument("--ib-tpn", type=int, default=0, help="threads per wall node of the node kernel (0: default 4)")
     ap.add_argument("--ib-slabs", type=int, default=0,
                     help="slabs of the pipelined wall-node step (0 or 1: one launch per kernel, the library's default)")
     return ap.parse_args()

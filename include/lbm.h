@@ -126,7 +126,7 @@ typedef struct {
     int graph_steps;   /* steps per captured CUDA graph (even, >= 2); 0 = 64 */
     int wave_capacity; /* waveform ring-buffer length in steps; 0 = 8192 */
     int block_size;    /* threads per block of the stream-collide kernel, multiple of 32 in [32, 256]; 0 = 128 */
-    int ib_threads_per_node; /* threads of the immersed-boundary node kernel per wall node: 1, 2 or 4; 0 = 2 */
+    int ib_threads_per_node; /* threads of the immersed-boundary node kernel per wall node: 1, 2 or 4; 0 = 4 */
     /* Pipelining of a step with wall nodes over slabs of lattice planes: the
      * band velocities, the wall-node kernel and stream-collide of neighbouring
      * slabs overlap on three streams (same arithmetic and results as one

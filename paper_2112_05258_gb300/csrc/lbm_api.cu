@@ -627,7 +627,7 @@ lbm_status lbm_create(const lbm_config *cfg, lbm_handle **out) {
     h->ibp.ks = h->ibks;
     h->ibp.pinned = h->ibpin;
     h->ibp.vband = h->vband;
-    h->ibp.threads_per_node = cfg->ib_threads_per_node ? cfg->ib_threads_per_node : 2;
+    h->ibp.threads_per_node = cfg->ib_threads_per_node ? cfg->ib_threads_per_node : 4;
     h->ibp.lines = h->iblines;
     h->ibp.mask = h->ibmask;
     h->ibp.ref = h->ibref;

@@ -93,7 +93,7 @@ __device__ __forceinline__ void vec_atomic_add(double4a *a, double4a v) {
 // The kernel takes the wall nodes ib.order[k0 .. k1) (all nodes in index
 // order when ib.order is null).
 //
-// With two threads per node, consecutive nodes (the pair k0 + 2m, k0 + 2m + 1,
+// With two or four threads per node, consecutive nodes (the pair k0 + 2m, k0 + 2m + 1,
 // neighbours on a ring, whose supports share about 70 % of their cells) merge
 // their spreading: the first node of the pair adds the second node's
 // contribution F' delta(x - X') dA' to every cell of its own support that
@@ -101,14 +101,14 @@ __device__ __forceinline__ void vec_atomic_add(double4a *a, double4a v) {
 // node spreads only into the cells outside the first one's support.  On the
 // aorta membrane this takes the atomics from 64 to about 42 per node.  The
 // partner's weights, reference cell and force come by shuffles within the
-// pair's four lanes; a pair whose supports do not overlap, or with a node out
+// pair's lanes; a pair whose supports do not overlap, or with a node out
 // of its band or past k1, spreads node by node.
 template <class S, int TPN>
 __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib, int k0, int k1) {
     using R = typename Storage<S>::R;
     using V = typename Vec4<R>::T;
     constexpr int PL = 4 / TPN;
-    constexpr bool PAIRED = TPN == 2;
+    constexpr bool PAIRED = TPN >= 2;
     const int gt = blockIdx.x * blockDim.x + threadIdx.x;
     const int kk = k0 + gt / TPN, q = gt % TPN;
     // the lanes of a node leave together; with pairs, those of a pair (a
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(128) k_ib_nodes(KParams p, IbKParams ib, int k
     R pw[3][4], pF[3] = {R(0), R(0), R(0)};
     uint32_t pin[3] = {0u, 0u, 0u};
     if (PAIRED) {
-        const unsigned pm = 0xFu << ((threadIdx.x & 31) & ~3u);
+        const unsigned pm = ((1u << (2 * TPN)) - 1u) << ((threadIdx.x & 31) & ~(2u * TPN - 1u));  // the pair's lanes
         const bool ok = !dead && !out_of_band;
         first = ((gt / TPN) & 1) == 0;
         const bool pok = __shfl_xor_sync(pm, (int)ok, TPN) != 0;
