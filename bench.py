@@ -12,7 +12,11 @@ interpolation/spreading and wall update, fused stream-collide with bounce-back,
 boundary flow/pressure reduction, 0D ODE step and non-equilibrium
 extrapolation.  ``value`` = fluid-cell updates per second (MLUPS) over all
 ranks, timed with CUDA events on the library's stream (inputs resident in HBM;
-the 611 MB population arrays exceed L2, so no flush is needed).
+the 611 MB population arrays exceed L2, so no flush is needed).  ``e2e`` =
+the same through the public API with per-step host I/O: lbm_step_io, whose
+step graphs read each step's outlet Windkessel parameters from pinned host
+memory and write each step's 0D state rows back to pinned host memory on the
+device (with, beside it, the figure for the same I/O as per-step host calls).
 
 ``--impl reference`` times the plain FP64 CPU oracle on the same workload
 (bounded sample of steps) and prints the same JSON line with impl=reference.
@@ -322,29 +326,45 @@ def main():
     peak, peak_src = measured_peaks()
     traffic = profiled_traffic() if (args.precision == "f32" and args.workload == "aorta") else None
 
-    # end to end through the public API: every step the host writes the outlet
-    # Windkessel parameters (H2D, staged in the handle's pinned ring) and reads
-    # the 0D state of all boundaries of the instance (D2H into pinned host
-    # memory, one row block per step), all stream-ordered; the host waits once
+    # end to end through the public API (lbm_step_io): every step the device
+    # reads that step's outlet Windkessel parameters from pinned host memory
+    # (H2D) and writes the 0D state of all boundaries of the instance into
+    # pinned host memory (D2H), in stream order inside the step graphs; the
+    # host waits once.  Beside it, the same through per-step host calls
+    # (lbm_set_0d_params, lbm_step(h, 1), lbm_read_0d_state_async).
     rcr = np.array(inst.boundaries[1].params, dtype=np.float64)
     nbc = len(inst.boundaries)
     e2e_steps = min(args.steps, 1000)
+    params = torch.from_numpy(np.tile(rcr, (e2e_steps, 1))).pin_memory()
     rows = torch.zeros((e2e_steps, 8 * nbc), dtype=torch.float64, pin_memory=True)
+    lat.step_io(0, 1, e2e_steps, params.data_ptr(), rcr.size, rows.data_ptr())  # captures the graphs
+    lat.sync()
     barrier()
     t0 = time.perf_counter()
-    for s in range(e2e_steps):
-        lat.set_0d_params(0, 1, rcr)
-        lat.step(1)
-        lat.state_0d_async(0, rows[s].data_ptr())
+    lat.step_io(0, 1, e2e_steps, params.data_ptr(), rcr.size, rows.data_ptr())
     lat.sync()
     barrier()
     e2e_s = max_over_ranks(time.perf_counter() - t0, world, device=f"cuda:{local}")
     step_of_rows = rows[:, 0].numpy()
     if not np.array_equal(np.diff(step_of_rows), np.ones(e2e_steps - 1)):
         raise RuntimeError("end-to-end read-back rows are not consecutive steps")
+    rows2 = torch.zeros((e2e_steps, 8 * nbc), dtype=torch.float64, pin_memory=True)
+    barrier()
+    t0 = time.perf_counter()
+    for s in range(e2e_steps):
+        lat.set_0d_params(0, 1, rcr)
+        lat.step(1)
+        lat.state_0d_async(0, rows2[s].data_ptr())
+    lat.sync()
+    barrier()
+    calls_s = max_over_ranks(time.perf_counter() - t0, world, device=f"cuda:{local}")
+    if not np.array_equal(np.diff(rows2[:, 0].numpy()), np.ones(e2e_steps - 1)):
+        raise RuntimeError("per-step read-back rows are not consecutive steps")
     e2e = {"value": replica_throughput(cells, e2e_steps, world, e2e_s * 1e3), "unit": "MLUPS",
            "h2d_bytes_per_step": int(rcr.nbytes), "d2h_bytes_per_step": int(8 * 8 * nbc),
-           "steps": e2e_steps}
+           "steps": e2e_steps, "api": "lbm_step_io",
+           "per_step_calls": {"value": replica_throughput(cells, e2e_steps, world, calls_s * 1e3), "unit": "MLUPS",
+                              "api": "lbm_set_0d_params + lbm_step(h, 1) + lbm_read_0d_state_async"}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ("aorta", "tube"):

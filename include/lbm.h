@@ -198,6 +198,25 @@ lbm_status lbm_init_populations(lbm_handle *h, int inst, const double *f);
  * remainder, single-step graphs (each captured once per step parity). */
 lbm_status lbm_step(lbm_handle *h, int64_t n);
 
+/* n steps with per-step 0D input and output and no host round trip: before
+ * step k (k = 0 .. n-1) the params of boundary bc of instance inst become
+ * params[k np .. k np + np) (as lbm_set_0d_params would set them: the
+ * boundary's time-varying input, e.g. an outlet resistance), and after it
+ * the 8-value state rows of every boundary of inst (the rows of
+ * lbm_read_0d_state_async, step count first) go to states[k 8 n_bc ..
+ * (k + 1) 8 n_bc).  Both arrays are caller-owned page-locked host memory that
+ * the device can address (cudaHostAlloc, or pinned allocations of a framework
+ * with unified addressing): the device reads each step's params and writes
+ * each step's rows there itself, in stream order, inside the same CUDA graphs
+ * that take the steps (graphs of graph_steps steps, cached per array pair,
+ * boundary and length), so no host call sits between the steps.  Asynchronous:
+ * returns after enqueueing; the rows are complete when lbm_sync returns, and
+ * the params must stay unchanged until then.  Every params set is validated
+ * on the host first (as lbm_set_0d_params); on return the host copy of the
+ * boundary's params is the last set.  LBM_ERR_ARG for a bad instance,
+ * boundary, count or params set, or arrays the device cannot address. */
+lbm_status lbm_step_io(lbm_handle *h, int inst, int bc, int64_t n, const double *params, int np, double *states);
+
 /* Waits for the stream; returns LBM_ERR_UNSTABLE if the device status word
  * recorded NaN/Inf or |v| > 0.3 (stream-collide) or a wall node more than one
  * cell from its reference cell, i.e. outside its immersed-boundary support

@@ -100,6 +100,16 @@ struct lbm_handle {
     cudaEvent_t ev_ofork = nullptr, ev_oband = nullptr, ev_obc = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     cudaGraphExec_t graph1[2] = {nullptr, nullptr};  // single steps (by parity), for step counts below graph_steps
+    // lbm_step_io: the call's step counter on the device, and its step graphs
+    // (each step with its 0D input and output kernels), keyed by the host
+    // arrays, the boundary, the graph length and the starting parity
+    long long *io_cursor = nullptr;
+    struct IoGraph {
+        const void *params, *states;
+        int np, inst, bc, len, parity;
+        cudaGraphExec_t exec;
+    };
+    std::vector<IoGraph> io_graphs;
     // kernel timing
     bool timing = false;
     std::vector<cudaEvent_t> ev;
@@ -358,6 +368,56 @@ lbm_status ensure_graph1(lbm_handle *h) {
     return LBM_OK;
 }
 
+// One step of lbm_step_io: the params of step *io_cursor, the step, the
+// state rows written after it.  band_done / next as in launch_step.
+lbm_status launch_io_step(lbm_handle *h, const double *params_dev, int np, int b, double *states_dev, int inst,
+                          bool timed, bool band_done, bool next) {
+    const InstParam &ip = h->L.inst[inst];
+    CK(h, launch_io_params(params_dev, np, &h->bc_par[b], h->io_cursor, h->stream));
+    lbm_status st = launch_step(h, timed, band_done, next);
+    if (st != LBM_OK) return st;
+    CK(h, launch_io_state(h->bc_state, h->bc_par, h->etab, ip.bc_first, ip.n_bc, (int)h->L.bc.size(), h->step_dev,
+                          states_dev, h->io_cursor, h->stream));
+    return LBM_OK;
+}
+
+// The cached lbm_step_io graph of len steps for these arrays and boundary,
+// starting at the current parity (captured on first use).
+lbm_status ensure_io_graph(lbm_handle *h, const double *params_dev, int np, int b, double *states_dev, int inst,
+                           int len, cudaGraphExec_t *out) {
+    for (auto &g : h->io_graphs)
+        if (g.params == params_dev && g.states == states_dev && g.np == np && g.inst == inst && g.bc == b &&
+            g.len == len && g.parity == h->parity) {
+            *out = g.exec;
+            return LBM_OK;
+        }
+    const int par = h->parity;
+    cudaGraph_t g = nullptr;
+    CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    lbm_status st = LBM_OK;
+    for (int k = 0; k < len && st == LBM_OK; k++)
+        st = launch_io_step(h, params_dev, np, b, states_dev, inst, false, k > 0 && h->overlap,
+                            k + 1 < len && h->overlap);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    h->parity = par;  // capture does not run anything
+    if (st != LBM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    CK(h, e);
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiateWithFlags(&exec, g, cudaGraphInstantiateFlagUseNodePriority);
+    cudaGraphDestroy(g);
+    CK(h, e);
+    if (h->io_graphs.size() >= 8) {  // a small cache: drop the oldest
+        cudaGraphExecDestroy(h->io_graphs.front().exec);
+        h->io_graphs.erase(h->io_graphs.begin());
+    }
+    h->io_graphs.push_back({params_dev, states_dev, np, inst, b, len, par, exec});
+    *out = exec;
+    return LBM_OK;
+}
+
 lbm_status read_gather(lbm_handle *h, int inst, bool with_f) {
     const size_t m = (size_t)h->max_inst_cells;
     if (with_f && !h->rd_f19) CK(h, dalloc(h, &h->rd_f19, 19 * m));
@@ -370,6 +430,8 @@ lbm_status read_gather(lbm_handle *h, int inst, bool with_f) {
 }
 
 void drop_graphs(lbm_handle *h) {
+    for (auto &g : h->io_graphs) cudaGraphExecDestroy(g.exec);
+    h->io_graphs.clear();
     for (int k = 0; k < 2; k++) {
         if (h->graph[k]) {
             cudaGraphExecDestroy(h->graph[k]);
@@ -383,6 +445,17 @@ void drop_graphs(lbm_handle *h) {
 }
 
 bool bad_inst(lbm_handle *h, int inst) { return !h || inst < 0 || inst >= (int)h->inst.size(); }
+
+// validation of one set of boundary params (lbm_set_0d_params, lbm_step_io); null if valid
+const char *bad_params(const BcParam &bp, const double *p, int np) {
+    static const int need[4] = {1, 4, 4, 1};
+    if (np < need[bp.kind]) return "too few params";
+    if (bp.kind == BC_RCR && (!(p[1] > 0) || !(p[2] > 0))) return "RCR needs C, R_d > 0";
+    if (bp.kind == BC_LV && ((int)p[0] != bp.period || !(p[2] > 0))) return "LV period is fixed at creation; N_S > 0";
+    if ((bp.kind == BC_RCR || bp.kind == BC_LV) && np >= 5 && !(p[4] == 0 || p[4] == 1 || p[4] == 2 || p[4] == 4))
+        return "0D scheme order must be 0, 1, 2 or 4";
+    return nullptr;
+}
 
 }  // namespace
 
@@ -686,13 +759,7 @@ lbm_status lbm_set_0d_params(lbm_handle *h, int inst, int bc, const double *p, i
     const InstParam &ip = h->L.inst[inst];
     if (bc < 0 || bc >= ip.n_bc || !p || np < 1 || np > 8) return fail(h, LBM_ERR_ARG, "bad boundary or params");
     BcParam &bp = h->L.bc[ip.bc_first + bc];
-    static const int need[4] = {1, 4, 4, 1};
-    if (np < need[bp.kind]) return fail(h, LBM_ERR_ARG, "too few params");
-    if (bp.kind == BC_RCR && (!(p[1] > 0) || !(p[2] > 0))) return fail(h, LBM_ERR_ARG, "RCR needs C, R_d > 0");
-    if (bp.kind == BC_LV && ((int)p[0] != bp.period || !(p[2] > 0)))
-        return fail(h, LBM_ERR_ARG, "LV period is fixed at creation; N_S > 0");
-    if ((bp.kind == BC_RCR || bp.kind == BC_LV) && np >= 5 && !(p[4] == 0 || p[4] == 1 || p[4] == 2 || p[4] == 4))
-        return fail(h, LBM_ERR_ARG, "0D scheme order must be 0, 1, 2 or 4");
+    if (const char *why = bad_params(bp, p, np)) return fail(h, LBM_ERR_ARG, why);
     for (int k = 0; k < np; k++) bp.par[k] = p[k];
     CK(h, cudaSetDevice(h->device));
     if (!h->par_ring) {
@@ -779,6 +846,55 @@ lbm_status lbm_step(lbm_handle *h, int64_t n) {
         h->parity = 1 - h->parity;
         h->steps++;
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_step_io(lbm_handle *h, int inst, int bc, int64_t n, const double *params, int np, double *states) {
+    if (bad_inst(h, inst)) return fail(h, LBM_ERR_ARG, "bad instance");
+    const InstParam &ip = h->L.inst[inst];
+    if (bc < 0 || bc >= ip.n_bc || !params || !states || np < 1 || np > 8 || n < 0)
+        return fail(h, LBM_ERR_ARG, "bad boundary, step count, params or state array");
+    if (n == 0) return LBM_OK;
+    const int b = ip.bc_first + bc;
+    BcParam &bp = h->L.bc[b];
+    for (int64_t k = 0; k < n; k++)
+        if (const char *why = bad_params(bp, params + k * np, np)) return fail(h, LBM_ERR_ARG, why);
+    CK(h, cudaSetDevice(h->device));
+    // both arrays must be page-locked host memory with a device address
+    const double *pdev = nullptr;
+    double *sdev = nullptr;
+    {
+        cudaPointerAttributes a{}, c{};
+        if (cudaPointerGetAttributes(&a, params) != cudaSuccess || a.type != cudaMemoryTypeHost || !a.devicePointer ||
+            cudaPointerGetAttributes(&c, states) != cudaSuccess || c.type != cudaMemoryTypeHost || !c.devicePointer) {
+            (void)cudaGetLastError();
+            return fail(h, LBM_ERR_ARG, "params and states must be page-locked host memory the device can address");
+        }
+        pdev = static_cast<const double *>(a.devicePointer);
+        sdev = static_cast<double *>(c.devicePointer);
+    }
+    if (!h->io_cursor) CK(h, dalloc(h, &h->io_cursor, 1));
+    CK(h, cudaMemsetAsync(h->io_cursor, 0, sizeof(long long), h->stream));
+    if (h->timing) {
+        for (int64_t k = 0; k < n; k++) {
+            lbm_status s = launch_io_step(h, pdev, np, b, sdev, inst, true, false, false);
+            if (s != LBM_OK) return s;
+            h->steps++;
+        }
+    } else {
+        int64_t left = n;
+        while (left > 0) {
+            const int len = (int)std::min<int64_t>(left, h->graph_steps);
+            cudaGraphExec_t g = nullptr;
+            lbm_status s = ensure_io_graph(h, pdev, np, b, sdev, inst, len, &g);
+            if (s != LBM_OK) return s;
+            CK(h, cudaGraphLaunch(g, h->stream));
+            if (len & 1) h->parity ^= 1;
+            h->steps += len;
+            left -= len;
+        }
+    }
+    for (int k = 0; k < np; k++) bp.par[k] = params[(n - 1) * np + k];  // the host copy: the last set
     return LBM_OK;
 }
 
@@ -1244,6 +1360,7 @@ void lbm_destroy(lbm_handle *h) {
         if (h->graph[k]) cudaGraphExecDestroy(h->graph[k]);
         if (h->graph1[k]) cudaGraphExecDestroy(h->graph1[k]);
     }
+    for (auto &g : h->io_graphs) cudaGraphExecDestroy(g.exec);
     for (auto e : h->ev) cudaEventDestroy(e);
     for (auto *v : {&h->ev_bm, &h->ev_node, &h->ev_sc})
         for (auto e : *v)

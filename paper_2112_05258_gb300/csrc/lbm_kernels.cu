@@ -462,15 +462,12 @@ cudaError_t launch_gather(int prec, const void *fin, const KParams &p, int c0, i
 
 // 0D state rows of boundaries [b0, b0 + nb) for lbm_read_0d_state_async:
 // {t, Q, Q_u, Pbar_gauge, state, C_v P_v (LV), valve_open, T_d}
-__global__ void k_state_rows(const BcState *__restrict__ st, const BcParam *__restrict__ par,
-                             const double *__restrict__ etab, int b0, int nb, int nbc_total, long long steps,
-                             double *out8) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nb) return;
-    const int b = b0 + k;
+// the 8-value state row of boundary b after `steps` steps
+__device__ __forceinline__ void state_row(const BcState *__restrict__ st, const BcParam *__restrict__ par,
+                                          const double *__restrict__ etab, int b, int nbc_total, long long steps,
+                                          double *o) {
     const BcState s = st[(size_t)(steps & 1) * nbc_total + b];
     const BcParam &P = par[b];
-    double *o = out8 + 8 * (size_t)k;
     o[0] = (double)steps;
     o[1] = s.Q;
     o[2] = s.Qu;
@@ -479,6 +476,47 @@ __global__ void k_state_rows(const BcState *__restrict__ st, const BcParam *__re
     o[5] = P.kind == BC_LV ? s.Pv / etab[2 * (P.etab_off + (int)(steps % P.period))] : 0.0;
     o[6] = s.valve_open;
     o[7] = s.Td;
+}
+
+__global__ void k_state_rows(const BcState *__restrict__ st, const BcParam *__restrict__ par,
+                             const double *__restrict__ etab, int b0, int nb, int nbc_total, long long steps,
+                             double *out8) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    state_row(st, par, etab, b0 + k, nbc_total, steps, out8 + 8 * (size_t)k);
+}
+
+// Per-step 0D input and output of lbm_step_io, in stream order around each
+// step.  *cursor counts the call's steps taken so far.  k_io_params copies the
+// np params of step *cursor (from page-locked host memory that the device
+// addresses) into the boundary's device parameters; k_io_state writes the
+// state rows of nb boundaries after the step (step count *step + 1, the step
+// index t_n of the step just taken plus one) to out8 + 8 nb *cursor and then
+// advances *cursor.
+__global__ void k_io_params(const double *__restrict__ params, int np, BcParam *par, const long long *cursor) {
+    const long long c = *cursor;
+    if ((int)threadIdx.x < np) par->par[threadIdx.x] = params[c * np + threadIdx.x];
+}
+
+__global__ void k_io_state(const BcState *__restrict__ st, const BcParam *__restrict__ par,
+                           const double *__restrict__ etab, int b0, int nb, int nbc_total,
+                           const long long *__restrict__ step, double *out8, long long *cursor) {
+    const long long c = *cursor;
+    const int k = threadIdx.x;
+    if (k < nb) state_row(st, par, etab, b0 + k, nbc_total, *step + 1, out8 + 8 * ((size_t)c * nb + k));
+    __syncthreads();
+    if (threadIdx.x == 0) *cursor = c + 1;
+}
+
+cudaError_t launch_io_params(const double *params, int np, BcParam *par, const long long *cursor, cudaStream_t s) {
+    k_io_params<<<1, 32, 0, s>>>(params, np, par, cursor);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_io_state(const BcState *st, const BcParam *par, const double *etab, int b0, int nb, int nbc_total,
+                            const long long *step, double *out8, long long *cursor, cudaStream_t s) {
+    k_io_state<<<1, 32 * ((nb + 31) / 32), 0, s>>>(st, par, etab, b0, nb, nbc_total, step, out8, cursor);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_state_rows(const BcState *st, const BcParam *par, const double *etab, int b0, int nb,

@@ -110,6 +110,10 @@ cudaError_t launch_wall_shear(int prec, const void *fin, const KParams &p, int c
 cudaError_t launch_state_rows(const BcState *st, const BcParam *par, const double *etab, int b0, int nb,
                               int nbc_total, long long steps, double *out8, cudaStream_t s);
 cudaError_t launch_copy_words(const void *src, void *dst, size_t bytes, cudaStream_t s);
+// per-step 0D input and output of lbm_step_io (see k_io_params, k_io_state)
+cudaError_t launch_io_params(const double *params, int np, BcParam *par, const long long *cursor, cudaStream_t s);
+cudaError_t launch_io_state(const BcState *st, const BcParam *par, const double *etab, int b0, int nb, int nbc_total,
+                            const long long *step, double *out8, long long *cursor, cudaStream_t s);
 cudaError_t launch_scatter_box(const double *mac4, int M, const int32_t *box, float *P, float *jx, float *jy,
                                float *jz, cudaStream_t s);
 cudaError_t launch_cycle_change(const BcKParams &q, const int *bc_first, const int *n_bc, const long long *period,

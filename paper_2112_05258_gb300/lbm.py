@@ -70,7 +70,7 @@ class LayoutStats(ctypes.Structure):
 EXPORTS = ["lbm_create", "lbm_set_0d_params", "lbm_init_populations", "lbm_step", "lbm_sync",
            "lbm_read_fields", "lbm_read_populations", "lbm_read_0d_state", "lbm_read_waveforms",
            "lbm_read_ib", "lbm_set_ib_state", "lbm_set_kernel_timing", "lbm_get_kernel_time",
-           "lbm_get_info", "lbm_last_error", "lbm_destroy", "lbm_boundary_flux_noalloc",
+           "lbm_get_info", "lbm_last_error", "lbm_destroy", "lbm_boundary_flux_noalloc", "lbm_step_io",
            "lbm_init_equilibrium", "lbm_set_0d_state", "lbm_cycle_change", "lbm_autotune",
            "lbm_wall_shear", "lbm_check_config", "lbm_checkpoint_size", "lbm_checkpoint_save",
            "lbm_checkpoint_load", "lbm_read_fields_device", "lbm_set_stream_collide_shape",
@@ -113,6 +113,8 @@ def load(path: Optional[str] = None):
     L.lbm_checkpoint_size.argtypes = [H, ctypes.POINTER(ctypes.c_int64)]
     L.lbm_set_stream_collide_shape.argtypes = [H, ctypes.c_int, ctypes.c_int]
     L.lbm_read_0d_state_async.argtypes = [H, ctypes.c_int, ctypes.c_void_p]
+    L.lbm_step_io.argtypes = [H, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int,
+                              ctypes.c_void_p]
     L.lbm_read_fields_device.argtypes = [H, ctypes.c_int] + [ctypes.c_void_p] * 4
     L.lbm_checkpoint_save.argtypes = [H, ctypes.c_void_p, ctypes.c_int64]
     L.lbm_checkpoint_load.argtypes = [H, ctypes.c_void_p, ctypes.c_int64]
@@ -377,6 +379,15 @@ class Lattice:
         inst into page-locked host memory at out_ptr (8 * n_bc doubles),
         filled when the lattice's stream reaches the call."""
         self._ck(load().lbm_read_0d_state_async(self._h, inst, ctypes.c_void_p(int(out_ptr))))
+
+    def step_io(self, inst: int, bc: int, n: int, params_ptr: int, n_params: int, states_ptr: int):
+        """n steps with per-step params of boundary bc of instance inst read from
+        page-locked host memory at params_ptr (n x n_params doubles) and the
+        0D state rows of every boundary of inst written to page-locked host
+        memory at states_ptr (n x 8 * n_bc doubles) after each step, all in
+        stream order on the device (lbm_step_io)."""
+        self._ck(load().lbm_step_io(self._h, int(inst), int(bc), int(n), ctypes.c_void_p(int(params_ptr)),
+                                    int(n_params), ctypes.c_void_p(int(states_ptr))))
 
     def set_stream_collide_shape(self, block: int, variant: int):
         """Fixes the stream-collide block size and variant (0..4)."""

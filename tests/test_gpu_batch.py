@@ -222,3 +222,72 @@ def test_once_per_boundary_0d_step_equals_per_block(Lattice):
         assert np.array_equal(big.waves(q), single.waves(0))
         assert np.array_equal(big.populations(q), single.populations(0))
         single.close()
+
+
+def _step_io_case(Lattice, inst, prec, n, start):
+    """Runs n steps of instance inst (after `start` plain steps) once through
+    lbm_step_io and once as per-step host calls (set the outlet params, one
+    step, asynchronous state read); returns both lattices and both row arrays."""
+    import torch
+    nbc = len(inst.boundaries)
+    base = np.array(inst.boundaries[1].params, dtype=np.float64)
+    params = torch.zeros((n, base.size), dtype=torch.float64, pin_memory=True)
+    for k in range(n):  # a time-varying outlet resistance R_p
+        params[k] = torch.from_numpy(base * np.array([1.0 + 0.3 * np.sin(2 * np.pi * k / 50.0)] +
+                                                     [1.0] * (base.size - 1)))
+    got = torch.full((n, 8 * nbc), -1.0, dtype=torch.float64, pin_memory=True)
+    a = Lattice([inst], precision=prec)
+    a.step(start)
+    a.step_io(0, 1, n, params.data_ptr(), base.size, got.data_ptr())
+    a.sync()
+    want = torch.full((n, 8 * nbc), -1.0, dtype=torch.float64, pin_memory=True)
+    b = Lattice([inst], precision=prec)
+    b.step(start)
+    for k in range(n):
+        b.set_0d_params(0, 1, params[k].numpy())
+        b.step(1)
+        b.state_0d_async(0, want[k].data_ptr())
+    b.sync()
+    return a, b, got.numpy(), want.numpy()
+
+
+def test_step_io_equals_per_step_calls(Lattice):
+    # per-step params read and state rows written by the device inside the
+    # step graphs (two graphs of 64 steps and a remainder of 22, starting at
+    # an odd step) equal the per-step host calls bit for bit on an instance
+    # without wall nodes; the rows carry consecutive step counts
+    a, b, got, want = _step_io_case(Lattice, configs.lv_tube(period=300), "f64", 150, 7)
+    assert np.array_equal(got, want)
+    assert np.array_equal(got[:, 0], np.arange(8, 158))
+    assert np.array_equal(a.populations(0), b.populations(0))
+    assert np.array_equal(a.waves(0), b.waves(0))
+    assert a.info().steps == b.info().steps == 157
+
+
+def test_step_io_with_wall_nodes(Lattice):
+    # with wall nodes the graphs also run the band velocities beside the
+    # boundary kernels: equal to the per-step calls to the rounding of the
+    # spreading atomics
+    for prec, tol in (("f64", 1e-14), ("f32", 1e-6)):
+        a, b, got, want = _step_io_case(Lattice, configs.ib_tube(), prec, 100, 3)
+        assert np.abs(got - want).max() <= tol * max(1.0, np.abs(want).max())
+        assert np.abs(a.populations(0) - b.populations(0)).max() < tol
+
+
+def test_step_io_rejects_bad_arguments(Lattice):
+    import torch
+    inst = configs.lv_tube(period=300)
+    lat = Lattice([inst], precision="f64")
+    rows = torch.zeros((4, 16), dtype=torch.float64, pin_memory=True)
+    pageable = np.zeros((4, 4))
+    pinned = torch.tensor(np.tile(inst.boundaries[1].params, (4, 1)), dtype=torch.float64).pin_memory()
+    with pytest.raises(RuntimeError):  # params in pageable host memory
+        lat.step_io(0, 1, 4, pageable.ctypes.data, 4, rows.data_ptr())
+    bad = pinned.clone().pin_memory()
+    bad[2, 1] = -1.0  # a compliance <= 0 in the third set
+    with pytest.raises(RuntimeError):
+        lat.step_io(0, 1, 4, bad.data_ptr(), 4, rows.data_ptr())
+    assert lat.info().steps == 0  # nothing was enqueued
+    lat.step_io(0, 1, 4, pinned.data_ptr(), 4, rows.data_ptr())
+    lat.sync()
+    assert lat.info().steps == 4
