@@ -105,7 +105,7 @@ struct BcDev {
 
 // grid: (ceil(nx / 256), nr), one row of the (x, r) grid per blockIdx.y
 template <class S>
-__global__ void __launch_bounds__(256) k_axi_collide(const S *__restrict__ fin, S *__restrict__ fout, Params p) {
+__global__ void __launch_bounds__(256, 8) k_axi_collide(const S *__restrict__ fin, S *__restrict__ fout, Params p) {
     using R = typename Storage<S>::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (x >= p.nx) return;
@@ -123,17 +123,17 @@ __global__ void __launch_bounds__(256) k_axi_collide(const S *__restrict__ fin, 
         else src = (uint32_t)(i * n + c - ex(i) - er(i) * p.nx);
         s[i] = Storage<S>::ld(fin + src);
     }
-    R sd = 0, jx = 0, jr = 0, pxr = 0, prr = 0;
+    // moments from the sums and differences of the four opposite pairs
+    // (1, 2) = +-e_x, (3, 4) = +-e_r, (5, 6) = +-(e_x + e_r), (7, 8) = +-(e_x - e_r)
+    R Sp[4], Dp[4];
 #pragma unroll
-    for (int i = 0; i < Q9; i++) {
-        sd += s[i];
-        if (ex(i)) jx += R(ex(i)) * s[i];
-        if (er(i)) {
-            jr += R(er(i)) * s[i];
-            prr += s[i];
-        }
-        if (ex(i) * er(i)) pxr += R(ex(i) * er(i)) * s[i];
+    for (int q = 0; q < 4; q++) {
+        Sp[q] = s[2 * q + 1] + s[2 * q + 2];
+        Dp[q] = s[2 * q + 1] - s[2 * q + 2];
     }
+    const R sd = s[0] + ((Sp[0] + Sp[1]) + (Sp[2] + Sp[3]));
+    const R jx = Dp[0] + Dp[2] + Dp[3], jr = Dp[1] + Dp[2] - Dp[3];
+    const R pxr = Sp[2] - Sp[3], prr = Sp[1] + Sp[2] + Sp[3];
     R omega, k, nu, inv_r;
     Consts<R>::get(p, j, &omega, &k, &nu, &inv_r);
     const R m = -jr * inv_r;
@@ -156,15 +156,26 @@ __global__ void __launch_bounds__(256) k_axi_collide(const S *__restrict__ fin, 
         aux[4 * n + c] = vr;
         aux[5 * n + c] = sd;
     }
-    const R usq = R(1.5) * vv, vg = vx * gx + vr * gr;
+    // BGK with f^eq_i - w_i = w_i (sp + 3 e.v + 9/2 (e.v)^2 - 3/2 v^2), the Guo
+    // term k w_i (3 (e - v).g + 9 (e.v)(e.g)) and the mass source k w_i m,
+    // k = 1 - 1/(2 tau), written per opposite pair (e.v and e.g change sign):
+    //   s*_i = (1 - omega) s_i + w (A + B),  s*_i' = (1 - omega) s_i' + w (A - B),
+    //   A = A0 + e.v (9/2 omega e.v + 9 k e.g),  B = 3 omega e.v + 3 k e.g,
+    //   A0 = omega (sp - 3/2 v^2) + k (m - 3 v.g)
+    const R om1 = R(1) - omega;
+    const R A0 = omega * (sp - R(1.5) * vv) + k * (m - R(3) * (vx * gx + vr * gr));
+    const R c45 = R(4.5) * omega, c9 = R(9) * k, c3w = R(3) * omega, c3k = R(3) * k;
+    const R eu[4] = {vx, vr, vx + vr, vx - vr};
+    const R eg[4] = {gx, gr, gx + gr, gx - gr};
+    Storage<S>::st(fout + (uint32_t)c, om1 * s[0] + R(4.0 / 9.0) * A0);
 #pragma unroll
-    for (int i = 0; i < Q9; i++) {
-        const R w = (R)wgt(i);
-        const R eu = R(ex(i)) * vx + R(er(i)) * vr;
-        const R eg = R(ex(i)) * gx + R(er(i)) * gr;
-        const R seq = w * (sp + R(3) * eu + R(4.5) * eu * eu - usq);
-        const R post = s[i] - omega * (s[i] - seq) + k * w * (R(3) * (eg - vg) + R(9) * eu * eg) + k * w * m;
-        Storage<S>::st(fout + ((uint32_t)i * (uint32_t)n + (uint32_t)c), post);  // 9 n < 2^31
+    for (int q = 0; q < 4; q++) {
+        const R w = q < 2 ? R(1.0 / 9.0) : R(1.0 / 36.0);
+        const R A = A0 + eu[q] * (c45 * eu[q] + c9 * eg[q]);
+        const R B = c3w * eu[q] + c3k * eg[q];
+        const int i = 2 * q + 1;
+        Storage<S>::st(fout + ((uint32_t)i * (uint32_t)n + (uint32_t)c), om1 * s[i] + w * (A + B));  // 9 n < 2^31
+        Storage<S>::st(fout + ((uint32_t)(i + 1) * (uint32_t)n + (uint32_t)c), om1 * s[i + 1] + w * (A - B));
     }
 }
 
