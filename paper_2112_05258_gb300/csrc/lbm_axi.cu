@@ -65,6 +65,7 @@ struct Params {
     double omega_d, k_d, nu_d;
     const float *inv_r_f;
     const double *inv_r_d;
+    long long *step;       // index t_n of the step in progress (advanced by the collide kernel)
 };
 
 template <class R> struct Consts;
@@ -100,7 +101,16 @@ struct BcDev {
     double *v0;                             // 2 per first-layer node
     double *wave;                           // ring [cap][1 + 4 n_bc]
     int wave_cap;
-    long long *step;                        // steps done
+    long long *step;                        // index t_n of the step in progress
+    // the boundary work of a step as two kernels: k_axi_bc_reduce (block k sums
+    // the first-layer chunk red_chunk[k] of boundary red_bc[k] into a partial)
+    // and k_axi_bc_apply (block k takes the 0D step of boundary app_bc[k] from
+    // the partials, summed in a fixed order, and writes the ghosts of its link
+    // chunk app_chunk[k]); state is [2][n_bc]: step t reads slot t & 1 and
+    // writes slot (t + 1) & 1
+    double *partial;                        // 2 per reduce block
+    const int32_t *red_bc, *red_chunk, *red_off, *red_n, *app_bc, *app_chunk;
+    int n_red_blocks, n_app_blocks;
 };
 
 // grid: (ceil(nx / 256), nr), one row of the (x, r) grid per blockIdx.y
@@ -108,6 +118,7 @@ template <class S>
 __global__ void __launch_bounds__(256, 8) k_axi_collide(const S *__restrict__ fin, S *__restrict__ fout, Params p) {
     using R = typename Storage<S>::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (p.step && x == 0 && j == 0) *p.step += 1;  // the step index t_n seen by the boundary kernels
     if (x >= p.nx) return;
     const int c = j * p.nx + x;
     const uint32_t fl = __ldg(&p.flags[c]);
@@ -245,99 +256,130 @@ __device__ __forceinline__ R dfeq_dev(int i, R sps, R vxs, R vrs, R spf, R vxf, 
                 R(1.5) * ((vxs * vxs + vrs * vrs) - (vxf * vxf + vrf * vrf)));
 }
 
-// All boundaries in one CTA (they are small in 2D): area-weighted FP64 sums
-// in a fixed tree order, the 0D step (t_n -> t_{n+1}), the waveform row, the
-// closure velocities, and the ghosts of Eq. Non-equilibrium3 written as
+// The 0D boundaries in two kernels.  k_axi_bc_reduce: block k sums, over
+// its chunk of BC2 first-layer nodes of boundary red_bc[k], the area-weighted
+// flow n.j / sum f and pressure deviation in FP64 (per-node terms in the
+// compute type), tree-reduced in shared memory, into partial[k].
+// k_axi_bc_apply: block k sums the partials of boundary app_bc[k] in their
+// fixed order on one thread, takes the 0D step (t_n -> t_{n+1}) there (every
+// link block of the boundary takes the same step from the same state slot,
+// same bits; its first block stores the new state and the waveform row), and
+// writes the ghosts of its chunk of links, Eq. Non-equilibrium3 written as
 //   f_i(x_b) = f*_i'(x_f) + f^eq_i'(P*, v*) - f^eq_i'(P(x_f), v(x_f)),
-// i' the direction arriving at x_f (mirrored for links across the axis).
-// Per-node and per-link terms run in the compute type R with pressures as
+// i' the direction arriving at x_f (mirrored for links across the axis).  A
+// valve closing in this step prescribes v_0(T_d) = v(x_f, T_d) per link
+// (links sharing x_f store the same closure velocity).  Pressures are
 // deviations from P_ref (the FP64 pipe of this part is narrow); the sums and
 // the 0D step are FP64.
+constexpr int BC2 = 256;
+
 template <class S>
-__global__ void __launch_bounds__(256) k_axi_bc(S *__restrict__ f, Params p, BcDev q) {
+__global__ void __launch_bounds__(BC2) k_axi_bc_reduce(Params p, BcDev q) {
     using R = typename Storage<S>::R;
     const R *aux = static_cast<const R *>(p.aux);
     const int n = p.n;
+    const int b = q.red_bc[blockIdx.x], ch = q.red_chunk[blockIdx.x];
+    const BcParam &P = q.par[b];
+    __shared__ double sQ[BC2], sP[BC2];
+    double Q = 0.0, Ps = 0.0;  // Ps: sum of A (P - P_ref)
+    const int a = ch * BC2 + threadIdx.x;
+    if (a < q.xf_n[b]) {
+        const int cf = q.xf[q.xf_off[b] + a];
+        const R A = (R)q.area[q.xf_off[b] + a];
+        Q = (double)(A * (R)P.sign * aux[n + cf] / (R(1) + aux[5 * n + cf]));
+        Ps = (double)(A * aux[cf] / R(3));
+    }
+    sQ[threadIdx.x] = Q;
+    sP[threadIdx.x] = Ps;
+    __syncthreads();
+    for (int st = BC2 / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) {
+            sQ[threadIdx.x] += sQ[threadIdx.x + st];
+            sP[threadIdx.x] += sP[threadIdx.x + st];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        q.partial[2 * blockIdx.x] = sQ[0];
+        q.partial[2 * blockIdx.x + 1] = sP[0];
+    }
+}
+
+template <class S>
+__global__ void __launch_bounds__(BC2) k_axi_bc_apply(S *__restrict__ f, Params p, BcDev q) {
+    using R = typename Storage<S>::R;
+    const R *aux = static_cast<const R *>(p.aux);
+    const int n = p.n;
+    const int b = q.app_bc[blockIdx.x], ch = q.app_chunk[blockIdx.x];
+    const BcParam &P = q.par[b];
     const long long t = *q.step;
-    __shared__ double sQ[256], sP[256];
     __shared__ double sh_Pstar, sh_S, sh_cos, sh_sin;
     __shared__ int sh_ptype, sh_closed;
-    const int width = 1 + 4 * q.n_bc;
-    double *row = q.wave + (size_t)(t % q.wave_cap) * width;
-    if (threadIdx.x == 0) row[0] = (double)t;
-    for (int b = 0; b < q.n_bc; b++) {
-        const BcParam &P = q.par[b];
-        double Q = 0.0, Ps = 0.0;  // Ps: sum of A (P - P_ref)
-        for (int a = threadIdx.x; a < q.xf_n[b]; a += blockDim.x) {
-            const int cf = q.xf[q.xf_off[b] + a];
-            const R A = (R)q.area[q.xf_off[b] + a];
-            Q += (double)(A * (R)P.sign * aux[n + cf] / (R(1) + aux[5 * n + cf]));
-            Ps += (double)(A * aux[cf] / R(3));
+    if (threadIdx.x == 0) {
+        double Q = 0.0, Ps = 0.0;
+        for (int k = 0; k < q.red_n[b]; k++) {  // the partials in their fixed order
+            Q += q.partial[2 * (q.red_off[b] + k)];
+            Ps += q.partial[2 * (q.red_off[b] + k) + 1];
         }
-        sQ[threadIdx.x] = Q;
-        sP[threadIdx.x] = Ps;
-        __syncthreads();
-        for (int s = 128; s > 0; s >>= 1) {
-            if ((int)threadIdx.x < s) {
-                sQ[threadIdx.x] += sQ[threadIdx.x + s];
-                sP[threadIdx.x] += sP[threadIdx.x + s];
-            }
-            __syncthreads();
+        int ptype, closed;
+        double Sm;
+        const double Psum = q.area_sum[b] / 3.0 + Ps;  // sum of A P over the layer
+        const BcState st = zero_d_step(P, q.state[(size_t)(t & 1) * q.n_bc + b], Q, Psum, q.area_sum[b], t, q.etab,
+                                       &ptype, &closed, &Sm);
+        sh_Pstar = st.Pstar_gauge;
+        sh_ptype = ptype;
+        sh_closed = closed;
+        sh_S = Sm;
+        if (P.kind == BC_VELOCITY) {  // the inlet's phase, once per block
+            const double w = P.par[0], tn1 = (double)(t + 1);
+            sh_cos = cos(w * tn1);
+            sh_sin = sin(w * tn1);
         }
-        if (threadIdx.x == 0) {
-            int ptype, closed;
-            double Sm;
-            const double Psum = q.area_sum[b] / 3.0 + sP[0];  // sum of A P over the layer
-            const BcState st = zero_d_step(P, q.state[b], sQ[0], Psum, q.area_sum[b], t, q.etab, &ptype, &closed, &Sm);
-            q.state[b] = st;
-            sh_Pstar = st.Pstar_gauge;
-            sh_ptype = ptype;
-            sh_closed = closed;
-            sh_S = Sm;
-            if (P.kind == BC_VELOCITY) {  // the inlet's phase, once for every link
-                const double w = P.par[0], tn1 = (double)(t + 1);
-                sh_cos = cos(w * tn1);
-                sh_sin = sin(w * tn1);
-            }
+        if (ch == 0) {
+            q.state[(size_t)((t + 1) & 1) * q.n_bc + b] = st;
+            const int width = 1 + 4 * q.n_bc;
+            double *row = q.wave + (size_t)(t % q.wave_cap) * width;
+            if (b == 0) row[0] = (double)t;
             row[1 + 4 * b] = st.Qu;
             row[2 + 4 * b] = st.Pbar - 1.0 / 3.0;
             row[3 + 4 * b] = P.kind == BC_RCR ? st.Pw : (P.kind == BC_LV ? st.Pv : st.Pstar_gauge);
             row[4 + 4 * b] = st.valve_open;
         }
-        __syncthreads();
-        if (sh_closed)
-            for (int a = threadIdx.x; a < q.xf_n[b]; a += blockDim.x) {
-                const int cf = q.xf[q.xf_off[b] + a];
-                q.v0[2 * (q.xf_off[b] + a)] = (double)aux[3 * n + cf];
-                q.v0[2 * (q.xf_off[b] + a) + 1] = (double)aux[4 * n + cf];
-            }
-        __syncthreads();
-        for (int L = threadIdx.x; L < q.lk_n[b]; L += blockDim.x) {
-            const int g = q.lk_off[b] + L;
-            const int cf = q.lk_xf[g], ie = q.lk_ieff[g];
-            const R spf = aux[cf], vxf = aux[3 * n + cf], vrf = aux[4 * n + cf];
-            R sps, vxs, vrs;
-            if (sh_ptype) {
-                sps = (R)(3.0 * sh_Pstar);  // 3 P* - 1 with P* = P_ref + P*_gauge
-                vxs = vxf;
-                vrs = vrf;
-            } else if (P.kind == BC_VELOCITY) {
-                const double *pr = q.profile + 3 * (size_t)(q.node_off[b] + q.lk_node[g]);
-                sps = spf;
-                vxs = (R)((double)P.sign * (pr[0] + pr[1] * sh_cos - pr[2] * sh_sin));
-                vrs = R(0);
-            } else {
-                const double *v0 = q.v0 + 2 * (size_t)(q.xf_off[b] + q.lk_xfi[g]);
-                sps = spf;
-                vxs = (R)(v0[0] * sh_S);
-                vrs = (R)(v0[1] * sh_S);
-            }
-            const R ghost = Storage<S>::ld(f + (size_t)ie * n + cf) + dfeq_dev<R>(ie, sps, vxs, vrs, spf, vxf, vrf);
-            Storage<S>::st(f + (size_t)q.lk_ib[g] * n + q.lk_xb[g], ghost);
-        }
-        __syncthreads();
     }
-    if (threadIdx.x == 0) *q.step = t + 1;
+    __syncthreads();
+    const int L = ch * BC2 + threadIdx.x;
+    if (L >= q.lk_n[b]) return;
+    const int g = q.lk_off[b] + L;
+    const int cf = q.lk_xf[g], ie = q.lk_ieff[g];
+    const R spf = aux[cf], vxf = aux[3 * n + cf], vrf = aux[4 * n + cf];
+    R sps, vxs, vrs;
+    if (sh_ptype) {
+        sps = (R)(3.0 * sh_Pstar);  // 3 P* - 1 with P* = P_ref + P*_gauge
+        vxs = vxf;
+        vrs = vrf;
+    } else if (P.kind == BC_VELOCITY) {
+        const double *pr = q.profile + 3 * (size_t)(q.node_off[b] + q.lk_node[g]);
+        sps = spf;
+        vxs = (R)((double)P.sign * (pr[0] + pr[1] * sh_cos - pr[2] * sh_sin));
+        vrs = R(0);
+    } else {
+        double *v0 = q.v0 + 2 * (size_t)(q.xf_off[b] + q.lk_xfi[g]);
+        double u0x, u0r;
+        if (sh_closed) {  // v_0(T_d) = v(x_f, T_d)
+            u0x = (double)vxf;
+            u0r = (double)vrf;
+            v0[0] = u0x;
+            v0[1] = u0r;
+        } else {
+            u0x = v0[0];
+            u0r = v0[1];
+        }
+        sps = spf;
+        vxs = (R)(u0x * sh_S);
+        vrs = (R)(u0r * sh_S);
+    }
+    const R ghost = Storage<S>::ld(f + (size_t)ie * n + cf) + dfeq_dev<R>(ie, sps, vxs, vrs, spf, vxf, vrf);
+    Storage<S>::st(f + (size_t)q.lk_ib[g] * n + q.lk_xb[g], ghost);
 }
 
 }  // namespace axi
@@ -418,6 +460,7 @@ Params params(const lbm_axi_handle *h) {
     p.nu_f = (float)p.nu_d;
     p.inv_r_f = h->inv_r_f;
     p.inv_r_d = h->inv_r_d;
+    p.step = h->d_step;
     return p;
 }
 
@@ -427,10 +470,16 @@ cudaError_t launch_step(lbm_axi_handle *h) {
     void *fin = h->f[h->parity], *fout = h->f[1 - h->parity];
     if (h->prec == LBM_F64) {
         k_axi_collide<double><<<grid, 256, 0, h->stream>>>(static_cast<const double *>(fin), static_cast<double *>(fout), p);
-        if (h->bd.n_bc) k_axi_bc<double><<<1, 256, 0, h->stream>>>(static_cast<double *>(fout), p, h->bd);
+        if (h->bd.n_bc) {
+            k_axi_bc_reduce<double><<<h->bd.n_red_blocks, BC2, 0, h->stream>>>(p, h->bd);
+            k_axi_bc_apply<double><<<h->bd.n_app_blocks, BC2, 0, h->stream>>>(static_cast<double *>(fout), p, h->bd);
+        }
     } else {
         k_axi_collide<float><<<grid, 256, 0, h->stream>>>(static_cast<const float *>(fin), static_cast<float *>(fout), p);
-        if (h->bd.n_bc) k_axi_bc<float><<<1, 256, 0, h->stream>>>(static_cast<float *>(fout), p, h->bd);
+        if (h->bd.n_bc) {
+            k_axi_bc_reduce<float><<<h->bd.n_red_blocks, BC2, 0, h->stream>>>(p, h->bd);
+            k_axi_bc_apply<float><<<h->bd.n_app_blocks, BC2, 0, h->stream>>>(static_cast<float *>(fout), p, h->bd);
+        }
     }
     h->parity = 1 - h->parity;
     return cudaGetLastError();
@@ -614,7 +663,8 @@ lbm_status lbm_axi_create(const lbm_axi_config *cfg, lbm_axi_handle **out) {
     if (aupload(h, &h->flags, flags) != cudaSuccess || aalloc(h, &aq, (size_t)6 * n * sb) != cudaSuccess ||
         cudaMemset(aq, 0, (size_t)6 * n * sb) != cudaSuccess || aalloc(h, &h->status, 1) != cudaSuccess ||
         cudaMemset(h->status, 0, sizeof(unsigned)) != cudaSuccess || aalloc(h, &h->d_step, 1) != cudaSuccess ||
-        cudaMemset(h->d_step, 0, sizeof(long long)) != cudaSuccess || aalloc(h, &h->rd, (size_t)12 * n) != cudaSuccess)
+        cudaMemset(h->d_step, 0xff, sizeof(long long)) != cudaSuccess ||  // -1: the first collide makes it t_0 = 0
+        aalloc(h, &h->rd, (size_t)12 * n) != cudaSuccess)
         return bail("out of memory");
     h->aux = aq;
     {
@@ -635,7 +685,31 @@ lbm_status lbm_axi_create(const lbm_axi_config *cfg, lbm_axi_handle **out) {
     BcState *dst;
     double *dv0, *dwave;
     const size_t width = 1 + 4 * std::max<size_t>(bcp.size(), 1);
-    bool ok = aupload(h, &dpar, bcp) == cudaSuccess && aupload(h, &dst, st) == cudaSuccess &&
+    std::vector<BcState> st2(st);  // both slots of the state start equal
+    st2.insert(st2.end(), st.begin(), st.end());
+    std::vector<int32_t> red_bc, red_chunk, red_off, red_n, app_bc, app_chunk;
+    for (size_t b = 0; b < bcp.size(); b++) {
+        const int nr = std::max(1, (xf_n[b] + BC2 - 1) / BC2), na = std::max(1, (lk_n[b] + BC2 - 1) / BC2);
+        red_off.push_back((int32_t)red_bc.size());
+        red_n.push_back(nr);
+        for (int k = 0; k < nr; k++) {
+            red_bc.push_back((int32_t)b);
+            red_chunk.push_back(k);
+        }
+        for (int k = 0; k < na; k++) {
+            app_bc.push_back((int32_t)b);
+            app_chunk.push_back(k);
+        }
+    }
+    double *dpart = nullptr;
+    bool ok = aupload(h, &dpar, bcp) == cudaSuccess && aupload(h, &dst, st2) == cudaSuccess &&
+              aupload(h, (int32_t **)&bd.red_bc, red_bc) == cudaSuccess &&
+              aupload(h, (int32_t **)&bd.red_chunk, red_chunk) == cudaSuccess &&
+              aupload(h, (int32_t **)&bd.red_off, red_off) == cudaSuccess &&
+              aupload(h, (int32_t **)&bd.red_n, red_n) == cudaSuccess &&
+              aupload(h, (int32_t **)&bd.app_bc, app_bc) == cudaSuccess &&
+              aupload(h, (int32_t **)&bd.app_chunk, app_chunk) == cudaSuccess &&
+              aalloc(h, &dpart, 2 * std::max<size_t>(red_bc.size(), 1)) == cudaSuccess &&
               aupload(h, (double **)&bd.etab, etab) == cudaSuccess &&
               aupload(h, (double **)&bd.profile, profile) == cudaSuccess &&
               aupload(h, (int32_t **)&bd.xf_off, xf_off) == cudaSuccess &&
@@ -658,6 +732,9 @@ lbm_status lbm_axi_create(const lbm_axi_config *cfg, lbm_axi_handle **out) {
     if (!ok) return bail("out of memory (boundaries)");
     bd.par = dpar;
     bd.state = dst;
+    bd.partial = dpart;
+    bd.n_red_blocks = (int)red_bc.size();
+    bd.n_app_blocks = (int)app_bc.size();
     bd.v0 = dv0;
     bd.wave = dwave;
     bd.wave_cap = h->wave_cap;
@@ -765,7 +842,8 @@ lbm_status lbm_axi_read_0d_state(lbm_axi_handle *h, int bc, double *out) {
     ACK(h, cudaSetDevice(h->device));
     ACK(h, cudaStreamSynchronize(h->stream));
     BcState s;
-    ACK(h, cudaMemcpy(&s, h->bd.state + bc, sizeof s, cudaMemcpyDeviceToHost));
+    ACK(h, cudaMemcpy(&s, h->bd.state + (size_t)(h->steps & 1) * h->bcp.size() + bc, sizeof s,
+                      cudaMemcpyDeviceToHost));  // the slot written by the last step
     const BcParam &bp = h->bcp[bc];
     out[0] = (double)h->steps;
     out[1] = s.Q;
