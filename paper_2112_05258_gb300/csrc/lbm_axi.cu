@@ -6,10 +6,11 @@
 //                  axisymmetric sources, Guo forcing, BGK collision
 //   k_axi_gather   read-out of f(t_n) and of P, u_x, u_r
 //   k_axi_init     inverse of the pull (lays out a given f(t_0))
-//   k_axi_bc       one CTA: for every 0D boundary the FP64 area-weighted
-//                  flow and pressure of its first fluid layer, the 0D step
-//                  and the ghost populations of Eq. Non-equilibrium3 (per
-//                  node and per link in the compute type)
+//   k_axi_bc_reduce  FP64 area-weighted flow and pressure partial sums over
+//                  chunks of every 0D boundary's first fluid layer
+//   k_axi_bc_apply   per chunk of links: the 0D step from the partials and
+//                  the ghost populations of Eq. Non-equilibrium3 (per node
+//                  and per link in the compute type)
 //
 // Sources (derived from the axisymmetric incompressible equations, rho0 = 1;
 // the printed h^(2) of Eq. AH1 is not legible): with j = sum e f (the
