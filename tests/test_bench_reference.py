@@ -36,3 +36,18 @@ def test_reference_arm_other_ranks_exit_without_work():
                        capture_output=True, text=True, timeout=300, cwd=ROOT, env=env)
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_launch_count_follows_the_step_graphs():
+    # lbm_step takes whole graphs of graph_steps steps, then single-step graphs;
+    # a graph's first step (and a single step) issues launches_first_step
+    # kernels, its later steps launches_per_step (the band velocities of the
+    # next step issued beside the boundary kernels)
+    sys.path.insert(0, ROOT)
+    import bench
+    from types import SimpleNamespace
+    info = SimpleNamespace(graph_steps=64, launches_first_step=5, launches_per_step=6)
+    assert bench.launches(info, 2000) == 31 * (5 + 63 * 6) + 16 * 5 == 11953
+    assert bench.launches(info, 64) == 5 + 63 * 6
+    assert bench.launches(info, 10) == 50
+    assert bench.launches(SimpleNamespace(graph_steps=8, launches_first_step=5, launches_per_step=5), 203) == 1015
