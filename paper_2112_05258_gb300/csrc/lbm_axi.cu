@@ -114,11 +114,13 @@ struct BcDev {
     int n_red_blocks, n_app_blocks;
 };
 
-// grid: (ceil(nx / 256), nr), one row of the (x, r) grid per blockIdx.y
+// grid: (x-blocks, nr) of 256 nodes of a row, one row of the (x, r) grid per
+// blockIdx.y; the launch covers the x-blocks xb0 .. xb0 + gridDim.x - 1
 template <class S>
-__global__ void __launch_bounds__(256, 8) k_axi_collide(const S *__restrict__ fin, S *__restrict__ fout, Params p) {
+__global__ void __launch_bounds__(256, 8) k_axi_collide(const S *__restrict__ fin, S *__restrict__ fout, Params p,
+                                                       int xb0) {
     using R = typename Storage<S>::R;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    const int x = (blockIdx.x + xb0) * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (p.step && x == 0 && j == 0) *p.step += 1;  // the step index t_n seen by the boundary kernels
     if (x >= p.nx) return;
     const int c = j * p.nx + x;
@@ -397,6 +399,13 @@ struct lbm_axi_handle {
     bool own_stream = false;
     int graph_steps = 64, wave_cap = 8192;
     cudaGraphExec_t graph = nullptr;
+    // Inside the step graph, the collide of the next step over the x-blocks
+    // that hold no first-layer node, [xb_lo, xb_hi) (they pull no ghost and
+    // write no aux), runs beside this step's boundary kernels (stream s_bc);
+    // the edge x-blocks follow the boundary kernels.  xb_hi = 0: no split.
+    int xb_lo = 0, xb_hi = 0;
+    cudaStream_t s_bc = nullptr;
+    cudaEvent_t ev_f = nullptr, ev_d = nullptr;
     int parity = 0;
     int64_t steps = 0;
     void *f[2] = {nullptr, nullptr};
@@ -465,25 +474,53 @@ Params params(const lbm_axi_handle *h) {
     return p;
 }
 
-cudaError_t launch_step(lbm_axi_handle *h) {
+template <class S> cudaError_t collide_blocks(lbm_axi_handle *h, const void *fin, void *fout, int b0, int b1,
+                                              cudaStream_t st) {
+    if (b1 <= b0) return cudaSuccess;
+    k_axi_collide<S><<<dim3(b1 - b0, h->nr), 256, 0, st>>>(static_cast<const S *>(fin), static_cast<S *>(fout),
+                                                         params(h), b0);
+    return cudaGetLastError();
+}
+
+template <class S> cudaError_t bc_kernels(lbm_axi_handle *h, void *fout, cudaStream_t st) {
+    if (!h->bd.n_bc) return cudaSuccess;
     const Params p = params(h);
-    const dim3 grid((h->nx + 255) / 256, h->nr);
+    k_axi_bc_reduce<S><<<h->bd.n_red_blocks, BC2, 0, st>>>(p, h->bd);
+    k_axi_bc_apply<S><<<h->bd.n_app_blocks, BC2, 0, st>>>(static_cast<S *>(fout), p, h->bd);
+    return cudaGetLastError();
+}
+
+// One step.  pre: the interior x-blocks of this step's collide were issued by
+// the previous step; next: issue the next step's interior x-blocks beside
+// this step's boundary kernels (graph capture only).
+template <class S> cudaError_t launch_step_t(lbm_axi_handle *h, bool pre, bool next) {
+    const int nbx = (h->nx + 255) / 256;
     void *fin = h->f[h->parity], *fout = h->f[1 - h->parity];
-    if (h->prec == LBM_F64) {
-        k_axi_collide<double><<<grid, 256, 0, h->stream>>>(static_cast<const double *>(fin), static_cast<double *>(fout), p);
-        if (h->bd.n_bc) {
-            k_axi_bc_reduce<double><<<h->bd.n_red_blocks, BC2, 0, h->stream>>>(p, h->bd);
-            k_axi_bc_apply<double><<<h->bd.n_app_blocks, BC2, 0, h->stream>>>(static_cast<double *>(fout), p, h->bd);
-        }
+    cudaError_t e = cudaSuccess;
+    if (pre) {  // the edge x-blocks, once the previous step's ghosts are in place
+        e = cudaStreamWaitEvent(h->stream, h->ev_d, 0);
+        if (e == cudaSuccess) e = collide_blocks<S>(h, fin, fout, 0, h->xb_lo, h->stream);
+        if (e == cudaSuccess) e = collide_blocks<S>(h, fin, fout, h->xb_hi, nbx, h->stream);
     } else {
-        k_axi_collide<float><<<grid, 256, 0, h->stream>>>(static_cast<const float *>(fin), static_cast<float *>(fout), p);
-        if (h->bd.n_bc) {
-            k_axi_bc_reduce<float><<<h->bd.n_red_blocks, BC2, 0, h->stream>>>(p, h->bd);
-            k_axi_bc_apply<float><<<h->bd.n_app_blocks, BC2, 0, h->stream>>>(static_cast<float *>(fout), p, h->bd);
-        }
+        e = collide_blocks<S>(h, fin, fout, 0, nbx, h->stream);
+    }
+    if (e != cudaSuccess) return e;
+    if (next) {
+        e = cudaEventRecord(h->ev_f, h->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->s_bc, h->ev_f, 0);
+        if (e == cudaSuccess) e = bc_kernels<S>(h, fout, h->s_bc);
+        if (e == cudaSuccess) e = cudaEventRecord(h->ev_d, h->s_bc);
+        // the next step reads fout and writes fin
+        if (e == cudaSuccess) e = collide_blocks<S>(h, fout, fin, h->xb_lo, h->xb_hi, h->stream);
+    } else {
+        e = bc_kernels<S>(h, fout, h->stream);
     }
     h->parity = 1 - h->parity;
-    return cudaGetLastError();
+    return e;
+}
+
+cudaError_t launch_step(lbm_axi_handle *h, bool pre = false, bool next = false) {
+    return h->prec == LBM_F64 ? launch_step_t<double>(h, pre, next) : launch_step_t<float>(h, pre, next);
 }
 
 // step counter for graph-free steps (the boundary kernel advances it when
@@ -740,6 +777,28 @@ lbm_status lbm_axi_create(const lbm_axi_config *cfg, lbm_axi_handle **out) {
     bd.wave = dwave;
     bd.wave_cap = h->wave_cap;
     bd.step = h->d_step;
+    if (!bcp.empty()) {
+        // x-blocks holding a first-layer node (the only nodes that pull ghosts
+        // or write aux) must wait for the boundary kernels; the rest may not
+        const int nbx = (nx + 255) / 256;
+        std::vector<uint8_t> edge((size_t)nbx, 0);
+        for (int32_t c : xf) edge[(size_t)((c % nx) / 256)] = 1;
+        int lo = 0, hi = nbx;
+        while (lo < nbx && edge[(size_t)lo]) lo++;
+        while (hi > lo && edge[(size_t)(hi - 1)]) hi--;
+        bool inner_clear = hi > lo;
+        for (int b = lo; b < hi; b++) inner_clear = inner_clear && !edge[(size_t)b];
+        if (inner_clear) {
+            int plo = 0, phi = 0;
+            if (cudaDeviceGetStreamPriorityRange(&plo, &phi) != cudaSuccess ||
+                cudaStreamCreateWithPriority(&h->s_bc, cudaStreamNonBlocking, phi) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->ev_f, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->ev_d, cudaEventDisableTiming) != cudaSuccess)
+                return bail("streams");
+            h->xb_lo = lo;
+            h->xb_hi = hi;
+        }
+    }
     if (cudaDeviceSynchronize() != cudaSuccess) return bail("initialisation failed");
     *out = h;
     return LBM_OK;
@@ -755,8 +814,9 @@ lbm_status lbm_axi_step(lbm_axi_handle *h, int64_t nsteps) {
             if (!h->graph) {
                 cudaGraph_t g;
                 ACK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+                const bool split = h->xb_hi > h->xb_lo;
                 for (int k = 0; k < h->graph_steps; k++) {
-                    cudaError_t e = launch_step(h);
+                    cudaError_t e = launch_step(h, split && k > 0, split && k + 1 < h->graph_steps);
                     if (e != cudaSuccess) {
                         cudaStreamEndCapture(h->stream, &g);
                         return afail(h, LBM_ERR_CUDA, cudaGetErrorString(e));
@@ -881,6 +941,10 @@ void lbm_axi_destroy(lbm_axi_handle *h) {
     if (!h) return;
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->s_bc) cudaStreamSynchronize(h->s_bc);
+    if (h->ev_f) cudaEventDestroy(h->ev_f);
+    if (h->ev_d) cudaEventDestroy(h->ev_d);
+    if (h->s_bc) cudaStreamDestroy(h->s_bc);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     for (void *p : h->allocs) cudaFree(p);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
